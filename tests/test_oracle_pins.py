@@ -1,0 +1,378 @@
+"""Pins of the FP64 CPU oracle against facts the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own formulas: closed forms
+(free-field plane waves), symmetries (gamma5-hermiticity, gauge covariance),
+dense linear algebra on tiny lattices (numpy LU / eig), the series form of the
+SAP preconditioner (Sec. 4) and the invariants of the Krylov layer (Eqs.
+"arnoldilike", "harmRitz", "hatHk", "r").
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import fieldgen as fg
+import oracle
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+G5 = np.array([1.0, 1.0, -1.0, -1.0])[None, :, None]
+
+
+def coords(dims):
+    V = fg.volume(dims)
+    return np.stack(np.unravel_index(np.arange(V), dims, order="F"), 1)
+
+
+def shift_index(dims, mu, sign):
+    c = coords(dims)
+    c[:, mu] = (c[:, mu] + sign) % dims[mu]
+    return np.ravel_multi_index(c.T, dims, order="F")
+
+
+# --------------------------------------------------------------------------- gamma basis
+def test_gamma_defining_relations():
+    g = [oracle.gamma(mu) for mu in range(4)]
+    for a in range(4):
+        assert np.allclose(g[a], g[a].conj().T)  # Hermitian
+        for b in range(4):
+            anti = g[a] @ g[b] + g[b] @ g[a]
+            assert np.allclose(anti, 2.0 * np.eye(4) * (a == b))
+    g5 = g[0] @ g[1] @ g[2] @ g[3]
+    assert np.allclose(g5, np.diag([1, 1, -1, -1]))
+
+
+# --------------------------------------------------------------------------- free field
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 8)])
+@pytest.mark.parametrize("m0", [-0.5, 0.3])
+def test_free_field_plane_waves(dims, m0):
+    """U = 1: plane wave e^{ip.n} u with (sum_j gamma_j sin p_j) u = s u is an
+    eigenvector of D with eigenvalue (4+m0) - sum_j cos p_j - i s."""
+    U = fg.unit_gauge(dims)
+    c = coords(dims)
+    g = [oracle.gamma(mu) for mu in range(4)]
+    rng = np.random.default_rng(7)
+    for _ in range(6):
+        kvec = [rng.integers(0, d) for d in dims]
+        p = np.array([2 * np.pi * kvec[j] / dims[j] for j in range(4)])
+        S = sum(g[j] * np.sin(p[j]) for j in range(4))
+        s_vals, s_vecs = np.linalg.eigh(S)
+        phase = np.exp(1j * (c @ p))
+        for a in range(4):
+            u = s_vecs[:, a]
+            colour = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+            psi = phase[:, None, None] * u[None, :, None] * colour[None, None, :]
+            lam = (4 + m0) - np.cos(p).sum() - 1j * s_vals[a]
+            out = oracle.dw(U, psi, dims, m0)
+            assert np.abs(out - lam * psi).max() < 1e-12 * max(1.0, np.abs(psi).max())
+
+
+def test_free_field_spectrum_closed_form():
+    """Dense free-field D on a 2x2x2x4 lattice: its spectrum is the closed form
+    with multiplicity 6 (12 when all sin p_j = 0)."""
+    dims = (2, 2, 2, 4)
+    m0 = -0.2
+    U = fg.unit_gauge(dims)
+    V = fg.volume(dims)
+    A = oracle.dense_operator(lambda v: oracle.dw(U, v.reshape(V, 4, 3), dims, m0).reshape(-1), 12 * V)
+    def canon(z):  # sort by rounded (re, im) so round-off cannot reorder equal values
+        z = np.asarray(z)
+        order = np.lexsort((np.round(z.imag, 8), np.round(z.real, 8)))
+        return z[order]
+
+    ev = canon(np.linalg.eigvals(A))
+    expect = []
+    for kvec in itertools.product(*[range(d) for d in dims]):
+        p = np.array([2 * np.pi * kvec[j] / dims[j] for j in range(4)])
+        s = np.sqrt((np.sin(p) ** 2).sum())
+        base = (4 + m0) - np.cos(p).sum()
+        expect += [base + 1j * s] * 6 + [base - 1j * s] * 6
+    expect = canon(np.array(expect))
+    assert np.abs(ev - expect).max() < 1e-10
+
+
+# --------------------------------------------------------------------------- symmetries
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2), (4, 2, 6, 2)])
+def test_gamma5_hermiticity(dims):
+    U = fg.gauge_field(dims, 0.5, seed=3)
+    psi = fg.gaussian_source(dims, 4)
+    phi = fg.gaussian_source(dims, 5)
+    m0 = -0.4
+    lhs = np.vdot(phi, G5 * oracle.dw(U, G5 * psi, dims, m0))
+    rhs = np.vdot(oracle.dw(U, phi, dims, m0), psi)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2)])
+def test_gauge_covariance(dims):
+    V = fg.volume(dims)
+    U = fg.gauge_field(dims, 0.6, seed=11)
+    psi = fg.gaussian_source(dims, 12)
+    g = fg.random_su3(V, 13)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        t = shift_index(dims, mu, +1)
+        Ug[:, mu] = g @ U[:, mu] @ g[t].conj().transpose(0, 2, 1)
+    m0 = 0.1
+    lhs = oracle.dw(Ug, np.einsum("sab,sxb->sxa", g, psi), dims, m0)
+    rhs = np.einsum("sab,sxb->sxa", g, oracle.dw(U, psi, dims, m0))
+    assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(rhs).max()
+
+
+def test_mass_shift():
+    dims = (4, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.4, seed=2)
+    psi = fg.gaussian_source(dims, 3)
+    d = oracle.dw(U, psi, dims, 0.37) - oracle.dw(U, psi, dims, 0.0)
+    assert np.abs(d - 0.37 * psi).max() < 1e-13
+
+
+def test_two_site_direction_sums_both_hops():
+    """d_j = 2: n + j and n - j are the same site, so both hop terms land on it
+    and D is the free-field closed form at p_j in {0, pi}."""
+    dims = (2, 4, 4, 4)
+    U = fg.unit_gauge(dims)
+    c = coords(dims)
+    p = np.array([np.pi, 0.0, np.pi / 2, 0.0])
+    psi = np.exp(1j * (c @ p))[:, None, None] * np.ones((1, 4, 3))
+    out = oracle.dw(U, psi, dims, 0.0)
+    g = [oracle.gamma(mu) for mu in range(4)]
+    S = sum(g[j] * np.sin(p[j]) for j in range(4))
+    expect = (4 - np.cos(p).sum()) * psi - 1j * np.einsum("ab,sbc->sac", S, psi)
+    assert np.abs(out - expect).max() < 1e-12
+
+
+# --------------------------------------------------------------------------- domains
+def _dense(U, dims, m0):
+    V = fg.volume(dims)
+    return oracle.dense_operator(lambda v: oracle.dw(U, v.reshape(V, 4, 3), dims, m0).reshape(-1), 12 * V)
+
+
+def _domain_index(dims, block):
+    c = coords(dims)
+    nb = [dims[j] // block[j] for j in range(4)]
+    dc = c // np.array(block)[None, :]
+    dom = dc[:, 0] + nb[0] * (dc[:, 1] + nb[1] * (dc[:, 2] + nb[2] * dc[:, 3]))
+    return dom, dc.sum(1) % 2
+
+
+SMALL_DIMS, SMALL_BLOCK = (4, 4, 2, 2), (2, 2, 1, 1)  # 64 sites, 16 domains of 4 sites
+
+
+def test_local_operator_is_principal_submatrix():
+    dims, block, m0 = SMALL_DIMS, SMALL_BLOCK, -0.5
+    U = fg.gauge_field(dims, 0.3, seed=0)
+    V = fg.volume(dims)
+    A = _dense(U, dims, m0)
+    Al = oracle.dense_operator(lambda v: oracle.dw_local(U, v.reshape(V, 4, 3), dims, block, m0).reshape(-1), 12 * V)
+    dom, col = _domain_index(dims, block)
+    sd = np.repeat(dom, 12)
+    same = sd[:, None] == sd[None, :]
+    assert np.abs(Al - np.where(same, A, 0)).max() < 1e-14
+    # the colouring: no coupling between distinct domains of the same colour (Sec. 2)
+    sc = np.repeat(col, 12)
+    cross_same_colour = (sc[:, None] == sc[None, :]) & ~same
+    assert np.abs(A[cross_same_colour]).max() == 0.0
+    assert np.array_equal(oracle.site_colours(dims, block), col)
+    assert col[0] == 0
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_sap_exact_local_solves_equal_series(s):
+    """SAP with exact domain solves, s cycles from 0, equals
+    M = sum_{j<s} (A_L^{-1} A_U)^j A_L^{-1} of the red-black block splitting
+    (Sec. 4; colour 0 is the leading block, swept first)."""
+    dims, block, m0 = (4, 4, 4, 2), (2, 2, 2, 1), -0.5
+    U = fg.gauge_field(dims, 0.3, seed=0)
+    V = fg.volume(dims)
+    A = _dense(U, dims, m0)
+    _, col = _domain_index(dims, block)
+    sc = np.repeat(col, 12)
+    perm = np.concatenate([np.where(sc == 0)[0], np.where(sc == 1)[0]])
+    Ap = A[np.ix_(perm, perm)]
+    h = (sc == 0).sum()
+    AL = Ap.copy()
+    AL[:h, h:] = 0
+    AU = -(Ap - AL)
+    ALi = np.linalg.inv(AL)
+    T = ALi @ AU
+    M = np.zeros_like(Ap)
+    P = np.eye(Ap.shape[0])
+    for _ in range(s):
+        M += P @ ALi
+        P = T @ P
+    v = fg.gaussian_source(dims, 21).reshape(-1)
+    z_series = np.empty_like(v)
+    z_series[perm] = M @ v[perm]
+    z = oracle.sap(U, v.reshape(V, 4, 3), dims, block, m0, s, 0).reshape(-1)
+    assert np.linalg.norm(z - z_series) <= 1e-11 * np.linalg.norm(z_series)
+
+
+def test_mr_monotone_and_converges_to_exact_local_solve():
+    dims, block, m0 = (4, 4, 4, 2), (2, 2, 2, 1), 2.0
+    U = fg.gauge_field(dims, 0.3, seed=0)
+    r = fg.gaussian_source(dims, 9)
+    norms, y = oracle.mr_history(U, r, dims, block, m0, 0, 60)
+    assert np.all(np.diff(norms) <= 1e-12 * norms[0])
+    V = fg.volume(dims)
+    col = oracle.site_colours(dims, block)
+    r0 = r * (col == 0)[:, None, None]
+    # exact block solve on colour 0 via the dense local operator
+    Al = oracle.dense_operator(lambda v: oracle.dw_local(U, v.reshape(V, 4, 3), dims, block, m0, 0).reshape(-1),
+                               12 * V)
+    mask = np.repeat(col == 0, 12)
+    y_exact = np.zeros(12 * V, dtype=np.complex128)
+    y_exact[mask] = np.linalg.solve(Al[np.ix_(mask, mask)], r0.reshape(-1)[mask])
+    assert np.linalg.norm(y.reshape(-1) - y_exact) <= 1e-8 * np.linalg.norm(y_exact)
+
+
+def test_sap_one_cycle_is_red_then_black_block_gauss_seidel():
+    """One SAP cycle with MR solves, written out with the local operator."""
+    dims, block, m0, nmr = (4, 4, 4, 4), (2, 2, 2, 2), -0.3, 3
+    U = fg.gauge_field(dims, 0.4, seed=1)
+    v = fg.gaussian_source(dims, 2)
+    col = oracle.site_colours(dims, block)
+    x = np.zeros_like(v)
+    for c in (0, 1):
+        r = v - oracle.dw(U, x, dims, m0)
+        r_c = r * (col == c)[:, None, None]
+        _, y = oracle.mr_history(U, r_c, dims, block, m0, c, nmr)
+        x = x + y * (col == c)[:, None, None]
+    z = oracle.sap(U, v, dims, block, m0, 1, nmr)
+    assert np.abs(z - x).max() < 1e-13 * np.abs(x).max()
+
+
+# --------------------------------------------------------------------------- Krylov layer
+def _tiny_system(seed=0):
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    U = fg.gauge_field(dims, 0.3, seed=seed)
+    return dims, block, U
+
+
+def test_flexible_arnoldi_relation_and_orthonormality():
+    dims, block, U = _tiny_system()
+    A, M = oracle.lattice_operators(U, dims, block, -0.5, 2, 2)
+    b = fg.gaussian_source(dims, 1).reshape(-1)
+    m = 12
+    V, Z, H = oracle.flexible_arnoldi(A, M, b, m)
+    AZ = np.stack([A(Z[j]) for j in range(m)])
+    assert np.linalg.norm(AZ - H.T @ V) <= 1e-12 * np.linalg.norm(AZ)
+    assert np.abs(V.conj() @ V.T - np.eye(m + 1)).max() < 1e-12
+    assert np.abs(np.tril(H, -2)).max() == 0.0
+
+
+def test_full_gmres_reaches_dense_solution():
+    """M = I, k = 0, m = n on a 2^4 lattice (n = 192): GMRES is exact."""
+    dims = (2, 2, 2, 2)
+    U = fg.gauge_field(dims, 0.5, seed=4)
+    V = fg.volume(dims)
+    m0 = -0.3
+    A = _dense(U, dims, m0)
+    b = fg.gaussian_source(dims, 5).reshape(-1)
+    x_star = np.linalg.solve(A, b)
+    Aop = lambda v: A @ v
+    res = oracle.fgmresdr(Aop, lambda v: v.copy(), b, 12 * V, 0, 1e-12)
+    assert res.converged and res.cycles == 1
+    assert np.linalg.norm(res.x - x_star) <= 1e-9 * np.linalg.norm(x_star)
+
+
+def test_exact_preconditioner_converges_in_one_step():
+    dims = (2, 2, 2, 2)
+    U = fg.gauge_field(dims, 0.5, seed=4)
+    A = _dense(U, dims, -0.3)
+    Ainv = np.linalg.inv(A)
+    b = fg.gaussian_source(dims, 6).reshape(-1)
+    res = oracle.fgmresdr(lambda v: A @ v, lambda v: Ainv @ v, b, 10, 3, 1e-11)
+    assert res.converged and res.iterations == 1
+
+
+def test_harmonic_ritz_lemma_1a():
+    """(A V_m)^H (A u - lambda u) = 0 for every harmonic Ritz pair (Eq. "harmRitz")."""
+    dims, block, U = _tiny_system()
+    A, _ = oracle.lattice_operators(U, dims, block, -0.5, 1, 1)
+    b = fg.gaussian_source(dims, 1).reshape(-1)
+    m = 15
+    V, Z, H = oracle.flexible_arnoldi(A, lambda v: v.copy(), b, m)
+    lam, G = oracle.harmonic_ritz(H)
+    AV = np.stack([A(V[j]) for j in range(m)])
+    for i in range(m):
+        u = G[:, i] @ V[:m]
+        resid = A(u) - lam[i] * u
+        assert np.abs(AV.conj() @ resid).max() <= 1e-10 * np.linalg.norm(resid) * np.linalg.norm(AV)
+
+
+def test_harmonic_ritz_values_approach_smallest_eigenvalues():
+    """M = I: after several deflated cycles the k harmonic Ritz values of
+    smallest modulus match the k eigenvalues of D nearest the origin."""
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 1.0, seed=2)
+    A0 = _dense(U, dims, 0.0)
+    ev0 = np.linalg.eigvals(A0)
+    m0 = 0.05 - ev0.real.min()
+    A = A0 + m0 * np.eye(A0.shape[0])
+    ev = ev0 + m0
+    near = ev[np.argsort(np.abs(ev))]
+    b = fg.gaussian_source(dims, 1).reshape(-1)
+    k = 3
+    res = oracle.fgmresdr(lambda v: A @ v, lambda v: v.copy(), b, 30, k, 1e-12, max_cycles=60)
+    assert res.converged and len(res.ritz) > 5
+    ritz = np.sort(np.abs(res.ritz[-1]))
+    assert np.allclose(ritz, np.sort(np.abs(near[:k])), rtol=1e-3)
+
+
+def test_deflated_restart_relation_hatHk():
+    """After the restart, A Z_k = V_{k+1} Hhat_k (Eqs. "hatHk", "tilde_Arnoldi")
+    and c = V_{k+1}^H r with r in span V_{k+1}."""
+    dims, block, U = _tiny_system()
+    A, M = oracle.lattice_operators(U, dims, block, -0.5, 2, 2)
+    b = fg.gaussian_source(dims, 1).reshape(-1)
+    m, k = 14, 4
+    V, Z, H = oracle.flexible_arnoldi(A, M, b, m)
+    c = np.zeros(m + 1, dtype=np.complex128)
+    c[0] = np.linalg.norm(b)
+    eta = np.linalg.lstsq(H, c, rcond=None)[0]
+    x = Z.T @ eta
+    r = b - A(x)
+    # the updated residual (Eq. "r") equals the explicit one
+    assert np.linalg.norm(V.T @ (c - H @ eta) - r) <= 1e-11 * np.linalg.norm(r)
+    Vk1, Zk, Hk, ck, _ = oracle.deflated_restart(V, Z, H, m, k, r)
+    AZk = np.stack([A(Zk[i]) for i in range(k)])
+    assert np.linalg.norm(AZk - Hk.T @ Vk1) <= 1e-10 * np.linalg.norm(AZk)
+    assert np.abs(Vk1.conj() @ Vk1.T - np.eye(k + 1)).max() < 1e-12
+    assert np.linalg.norm(Vk1.T @ ck - r) <= 1e-10 * np.linalg.norm(r)
+
+
+def test_residuals_monotone_and_consistent():
+    dims, block, U = _tiny_system()
+    b = fg.gaussian_source(dims, 1)
+    res = oracle.solve(U, b, dims, block, -0.5, 4, 4, 20, 5, 1e-12)
+    assert res.converged
+    expl = [h[2] for h in res.history]
+    assert all(b_ <= a_ * (1 + 1e-9) for a_, b_ in zip(expl, expl[1:]))
+    for _, impl, ex in res.history:
+        assert abs(impl - ex) <= 1e-6 * ex + 1e-14
+    assert res.true_rel_res <= 1e-12
+
+
+def test_deflation_reduces_iterations_near_critical():
+    """Sec. 5: at fixed m, deflation needs fewer matrix-vector products, most
+    visibly near the critical mass."""
+    dims, block = (4, 4, 2, 2), (2, 2, 1, 1)
+    U = fg.gauge_field(dims, 0.5, seed=0)
+    ev = np.linalg.eigvals(_dense(U, dims, 0.0))
+    m0 = 0.01 - ev.real.min()
+    b = fg.gaussian_source(dims, 1)
+    plain = oracle.solve(U, b, dims, block, m0, 1, 2, 8, 0, 1e-10, max_cycles=400)
+    defl = oracle.solve(U, b, dims, block, m0, 1, 2, 8, 3, 1e-10, max_cycles=400)
+    assert defl.converged
+    assert defl.iterations < plain.iterations
+
+
+def test_tune_m0_places_smallest_eigenvalue():
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.5, seed=0)
+    m0, vals, _ = oracle.tune_m0(U, dims, 1e-2, nev=4, ncv=40, tol=1e-10)
+    ev = np.linalg.eigvals(_dense(U, dims, m0))
+    # the leftmost eigenvalue of D_0 sits at Re = target after the shift
+    assert abs(ev.real.min() - 1e-2) < 1e-6
