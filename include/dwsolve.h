@@ -1,0 +1,172 @@
+/*
+ * dwsolve.h -- C ABI of the GB300 library for the Wilson-Dirac system D x = b
+ * solved by SAP-preconditioned flexible GMRES with deflated restarts.
+ *
+ * Operator (Sec. 2, Eq. "Dw" of Frommer, Nobile, Zingler, arXiv:1204.5463),
+ * written with a bare mass m0:
+ *     (D psi)_n = (4 + m0) psi_n
+ *                 - 1/2 sum_{j=1..4} [ (1 + gamma_j) U_{n,j} psi_{n+j}
+ *                                     + (1 - gamma_j) U^dagger_{n-j,j} psi_{n-j} ]
+ * with periodic boundaries in all four directions. This is the paper's
+ * D = 1 - kappa H_hop divided by 2 kappa, kappa = 1 / (2 (4 + m0)).
+ * Gamma matrices: Hermitian chiral basis, gamma_k = [[0, -i sigma_k],
+ * [i sigma_k, 0]] (k = 1..3), gamma_4 = [[0, 1], [1, 0]], so that
+ * gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1, 1, -1, -1).
+ *
+ * Canonical layouts at this boundary (FP64, complex numbers interleaved re,im):
+ *   site index   n = n1 + d1*(n2 + d2*(n3 + d3*n4)),  V = d1 d2 d3 d4
+ *   spinor field psi[rhs][site][spin 0..3][colour 0..2]  (24 doubles per site)
+ *   gauge field  U[site][mu 0..3][row 0..2][col 0..2]    (72 doubles per site)
+ * Buffers are owned by the caller; the library keeps its own converted copies
+ * of the gauge field and its own Krylov workspace, owned by the context.
+ *
+ * Every call returns DW_OK (0) or a DW_E* code; dw_last_error() gives a
+ * message for the calling thread. No C++ exception crosses this boundary.
+ * All device work of a context is issued on the CUDA stream given to
+ * dw_create; calls return after that work has completed unless stated.
+ */
+#ifndef DWSOLVE_H
+#define DWSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DW_OK 0
+#define DW_EINVAL 1       /* invalid argument (sizes, layout, parameters)       */
+#define DW_ECUDA 2        /* CUDA runtime error                                 */
+#define DW_ENOMEM 3       /* device allocation or HBM budget exhausted          */
+#define DW_ENOTCONV 4     /* solver stopped at max_cycles / max_iterations      */
+#define DW_EBREAKDOWN 5   /* unrecoverable breakdown of the Krylov process      */
+#define DW_ENONFINITE 6   /* NaN or Inf met in the residual or the Hessenberg   */
+#define DW_ETIMEOUT 7     /* a bounded device wait or a request deadline expired */
+#define DW_ECANCELLED 8   /* request cancelled                                   */
+
+#define DW_MAX_RHS 16
+
+/* Storage / arithmetic precision of a field or a kernel:
+ *   DW_F64  FP64 storage, FP64 arithmetic
+ *   DW_F32  FP32 storage, FP32 arithmetic
+ *   DW_F16  FP16 storage with one FP32 scale per site, FP32 arithmetic
+ *   DW_BF16 BF16 storage with one FP32 scale per site, FP32 arithmetic  */
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3 } dw_prec;
+
+/* Lattice L = {0 <= n <= d-1} (Sec. 2) and its decomposition into domains
+ * L^l of block[] sites each. Requirements: dims[j] >= 2; block[j] >= 1;
+ * dims[j] % block[j] == 0 and dims[j] / block[j] even (red-black colouring
+ * without same-colour coupling, Sec. 2 / Fig. 1); block volume <= 1024. */
+typedef struct {
+    int dims[4];
+    int block[4];
+    double m0;
+} dw_lattice;
+
+typedef struct dw_ctx dw_ctx;
+
+/* Create a context on the current CUDA device. cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) on which every launch of the context goes.
+ * Errors: DW_EINVAL for an invalid lattice, DW_ECUDA. */
+int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out);
+
+/* Release all device memory of the context. NULL is accepted. */
+void dw_destroy(dw_ctx* ctx);
+
+/* Change the bare mass m0 (keeps the gauge field). */
+int dw_set_mass(dw_ctx* ctx, double m0);
+
+/* Load the gauge field U (canonical FP64 layout, V*72 doubles). on_device
+ * selects a device (1) or host (0) pointer. The library converts it to its
+ * internal storage precisions on first use; the caller's buffer is not kept. */
+int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device);
+
+/* out = D in for nrhs spinor fields (Sec. 2, Eq. "Dw").
+ * in, out: device pointers, canonical FP64 layout, nrhs*V*24 doubles each,
+ * non-overlapping. prec selects the storage and arithmetic of the stencil:
+ * the input is rounded to prec, D is applied in prec, and the result (in
+ * prec storage) is widened back to FP64. 1 <= nrhs <= DW_MAX_RHS. */
+int dw_apply(dw_ctx* ctx, const double* in, double* out, dw_prec prec, int nrhs);
+
+/* z = M v with M the SAP preconditioner (Sec. 4): ncycles iterations of
+ * Algorithm 2 started from x = 0, each a sweep over the domains of colour 0
+ * (block coordinates summing to an even number; contains site 0) followed by
+ * colour 1. Each domain solve computes r = (v - D x)^l with the full
+ * operator, runs nmr minimal-residual steps on D^l y = r from y = 0 (Sec. 3)
+ * and adds x^l += y^l. storage selects the precision of v, x and the links
+ * (arithmetic FP32 for DW_F32/F16/BF16, FP64 for DW_F64).
+ * v, z: device pointers, canonical FP64 layout, nrhs fields each.
+ * Requires ncycles >= 1, nmr >= 1. */
+int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int nmr, dw_prec storage, int nrhs);
+
+typedef struct {
+    int m;                  /* basis dimension per cycle (Algorithm 4's m); 1 <= m <= 63   */
+    int k;                  /* deflation dimension (harmonic Ritz vectors); 0 <= k < m;
+                               k = 0 gives restarted FGMRES(m)                             */
+    double tol;             /* stop when ||b - D x||_2 / ||b||_2 <= tol (explicit, FP64)   */
+    int max_cycles;         /* limit on restart cycles                                     */
+    int max_iterations;     /* limit on Arnoldi steps (0 = none)                           */
+    int sap_cycles;         /* SAP iterations per preconditioner application               */
+    int mr_steps;           /* MR steps per domain solve                                   */
+    dw_prec sap_prec;       /* storage precision of SAP fields and of the Z basis          */
+    dw_prec matvec_prec;    /* precision of the Arnoldi product w = D z (DW_F64 or DW_F32) */
+    double clean_restart_t; /* clean restart when ||r_explicit|| / ||r_implicit|| > t (Sec. 4.5) */
+    int nrhs;               /* right-hand sides solved together, 1..DW_MAX_RHS             */
+    int host_buffers;       /* 1: b and x are host pointers (copies inside the call)       */
+    int use_x0;             /* 1: x holds the initial guess; 0: x0 = 0                     */
+} dw_solver_params;
+
+typedef struct {
+    int iterations;                  /* Arnoldi steps (= preconditioned matvecs), max over rhs */
+    int cycles;                      /* restart cycles, max over rhs                          */
+    int clean_restarts;              /* summed over rhs                                       */
+    int converged;                   /* number of rhs that met tol                            */
+    int explicit_residuals;          /* FP64 residual evaluations                             */
+    int iterations_rhs[DW_MAX_RHS];
+    double true_rel_res[DW_MAX_RHS]; /* final ||b - D x|| / ||b|| per rhs (FP64)             */
+    double time_s;                   /* wall time of the call                                 */
+} dw_stats;
+
+/* Defaults: m = 30, k = 10, tol = 1e-10, max_cycles = 500, max_iterations = 0,
+ * sap_cycles = 5, mr_steps = 4, sap_prec = DW_F32, matvec_prec = DW_F32,
+ * clean_restart_t = 4, nrhs = 1, host_buffers = 0, use_x0 = 0. */
+void dw_default_params(dw_solver_params* P);
+
+/* Solve D x = b for nrhs right-hand sides with FGMRES-DR (Algorithm 4):
+ * flexible Arnoldi (Algorithm 3) with classical Gram-Schmidt and selective
+ * reorthogonalisation in FP64, Givens-updated implicit residual (Sec. 4.4),
+ * harmonic Ritz deflation (Lemma 1a, Eqs. "G_kplus1", "hatHk"), and the
+ * refinement scheme of Sec. 4.5: every cycle recomputes r = b - D x in FP64 and
+ * injects it into the least-squares right-hand side, the last column of
+ * G_{k+1} and v_{k+1}; a clean restart follows when
+ * ||r_explicit|| / ||r_implicit|| > clean_restart_t.
+ * b, x: canonical FP64 layout, nrhs fields, device pointers unless
+ * P->host_buffers. Returns DW_OK when every rhs met tol, DW_ENOTCONV when a
+ * limit stopped the solve (x then holds the last iterate), or an error code.
+ * S may be NULL. */
+int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* dw_last_error(void);
+
+/* ---- measurement hooks ----------------------------------------------------
+ * While profiling is on, the context brackets its kernel launches with CUDA
+ * events on its stream and accumulates, per kernel class, the number of
+ * launches, the summed device time and the summed algorithmic bytes. */
+typedef struct {
+    char name[32];
+    long long launches;
+    double total_ms;
+    double bytes;
+} dw_kernel_stat;
+
+int dw_profile(dw_ctx* ctx, int enable);
+/* Copies up to max entries into out, sets *n; reset != 0 clears the totals. */
+int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWSOLVE_H */

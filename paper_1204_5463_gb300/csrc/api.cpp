@@ -1,0 +1,341 @@
+// C ABI of the library (include/dwsolve.h): contexts, the operator, the
+// preconditioner, the solver entry point, error reporting and profiling.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dense.h"
+#include "internal.h"
+
+namespace dwk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int DevBuf::ensure(size_t n) {
+    if (n <= bytes && p) return DW_OK;
+    release();
+    if (n == 0) return DW_OK;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return fail(DW_ENOMEM, std::string("cudaMalloc of ") + std::to_string(n) + " bytes failed: " +
+                                   cudaGetErrorString(e));
+    }
+    bytes = n;
+    return DW_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+// ---------------------------------------------------------------------------
+int Profiler::begin(const char* name, double bytes, cudaEvent_t* start_out, int* idx) {
+    int i = 0;
+    for (; i < (int)k.size(); ++i)
+        if (k[i].name == name) break;
+    if (i == (int)k.size()) {
+        k.emplace_back();
+        k.back().name = name;
+    }
+    cudaEvent_t a;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    cudaEventRecord(a, stream);
+    *start_out = a;
+    *idx = i;
+    k[i].pending_bytes.push_back(bytes);
+    return 0;
+}
+
+void Profiler::end(int idx, cudaEvent_t start) {
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(b, stream);
+    k[idx].pending.push_back({start, b});
+}
+
+void Profiler::drain() {
+    for (auto& e : k) {
+        for (size_t i = 0; i < e.pending.size(); ++i) {
+            cudaEventSynchronize(e.pending[i].second);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e.pending[i].first, e.pending[i].second);
+            e.total_ms += ms;
+            e.launches += 1;
+            e.bytes += (i < e.pending_bytes.size()) ? e.pending_bytes[i] : 0.0;
+            cudaEventDestroy(e.pending[i].first);
+            cudaEventDestroy(e.pending[i].second);
+        }
+        e.pending.clear();
+        e.pending_bytes.clear();
+    }
+}
+
+void Profiler::reset() {
+    drain();
+    k.clear();
+}
+
+Profiler::~Profiler() {
+    for (auto& e : k)
+        for (auto& p : e.pending) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+}
+
+// ---------------------------------------------------------------------------
+int gauge_for(dw_ctx* ctx, int prec, const char** out) {
+    if (!ctx->have_gauge) return fail(DW_EINVAL, "gauge field not set");
+    if (prec < 0 || prec > 3) return fail(DW_EINVAL, "bad precision");
+    if (!ctx->U_ready[prec]) {
+        int rc = ctx->U[prec].ensure((size_t)link_bytes(prec, ctx->g.V));
+        if (rc) return rc;
+        rc = launch_link_convert(prec, ctx->U[P64].as<char>(), ctx->U[prec].as<char>(), ctx->g.V, ctx->stream);
+        if (rc) return rc;
+        ctx->U_ready[prec] = true;
+    }
+    *out = ctx->U[prec].as<char>();
+    return DW_OK;
+}
+
+static int check_prec(int p) { return (p >= 0 && p <= 3) ? DW_OK : fail(DW_EINVAL, "bad precision"); }
+
+}  // namespace dwk
+
+using namespace dwk;
+
+extern "C" {
+
+const char* dw_last_error(void) { return g_err.c_str(); }
+
+int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out) {
+    if (!L || !out) return fail(DW_EINVAL, "null argument");
+    *out = nullptr;
+    Geom g;
+    g.V = 1;
+    g.B = 1;
+    g.ndom = 1;
+    for (int j = 0; j < 4; ++j) {
+        const int d = L->dims[j], b = L->block[j];
+        if (d < 2) return fail(DW_EINVAL, "lattice extent must be >= 2");
+        if (b < 1 || d % b != 0) return fail(DW_EINVAL, "block must divide the lattice extent");
+        if ((d / b) % 2 != 0) return fail(DW_EINVAL, "domain count per direction must be even (red-black)");
+        g.d[j] = d;
+        g.b[j] = b;
+        g.nb[j] = d / b;
+        g.V *= d;
+        g.B *= b;
+        g.ndom *= d / b;
+    }
+    if (g.B > 1024) return fail(DW_EINVAL, "domain volume must be <= 1024 sites");
+    if (g.V > (1LL << 31) / 24) return fail(DW_EINVAL, "lattice too large");
+    dw_ctx* c = new (std::nothrow) dw_ctx();
+    if (!c) return fail(DW_ENOMEM, "host allocation failed");
+    c->g = g;
+    c->m0 = L->m0;
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    c->prof.stream = c->stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return fail(DW_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    c->sap_threads.assign(4, 0);
+    *out = c;
+    return DW_OK;
+}
+
+void dw_destroy(dw_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    release_workspace(ctx->ws);
+    delete ctx;
+}
+
+int dw_set_mass(dw_ctx* ctx, double m0) {
+    if (!ctx) return fail(DW_EINVAL, "null context");
+    ctx->m0 = m0;
+    return DW_OK;
+}
+
+int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device) {
+    if (!ctx || !U) return fail(DW_EINVAL, "null argument");
+    const size_t bytes = (size_t)ctx->g.V * 72 * sizeof(double);
+    int rc = ctx->U[P64].ensure((size_t)link_bytes(P64, ctx->g.V));
+    if (rc) return rc;
+    const double* src = U;
+    if (!on_device) {
+        if ((rc = ctx->work_aux.ensure(bytes))) return rc;
+        DW_CUDA_TRY(cudaMemcpyAsync(ctx->work_aux.p, U, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->work_aux.as<double>();
+    }
+    if ((rc = launch_gauge_convert(P64, src, ctx->U[P64].as<char>(), ctx->g.V, ctx->stream))) return rc;
+    for (int p = 0; p < 4; ++p) ctx->U_ready[p] = false;
+    ctx->U_ready[P64] = true;
+    ctx->have_gauge = true;
+    DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return DW_OK;
+}
+
+int dw_apply(dw_ctx* ctx, const double* in, double* out, dw_prec prec, int nrhs) {
+    if (!ctx || !in || !out) return fail(DW_EINVAL, "null argument");
+    if (check_prec(prec)) return DW_EINVAL;
+    if (nrhs < 1 || nrhs > DW_MAX_RHS) return fail(DW_EINVAL, "nrhs out of range");
+    const long long V = ctx->g.V;
+    const long long fb = spinor_bytes(prec, V);
+    int rc;
+    const char* U;
+    if ((rc = gauge_for(ctx, prec, &U))) return rc;
+    if ((rc = ctx->work_in.ensure((size_t)nrhs * fb))) return rc;
+    if ((rc = ctx->work_out.ensure((size_t)nrhs * fb))) return rc;
+    if ((rc = launch_to_internal(prec, in, ctx->work_in.as<char>(), V, nrhs, ctx->stream))) return rc;
+    {
+        ProfScope ps(&ctx->prof, prec == DW_F64 ? "dw_f64" : prec == DW_F32 ? "dw_f32" : "dw_f16",
+                     (double)nrhs * (2.0 * fb + link_bytes(prec, V)));
+        FieldRef fi{ctx->work_in.as<char>(), fb, 0, 0}, fo{ctx->work_out.as<char>(), fb, 0, 0};
+        if ((rc = launch_dw(prec, prec, prec, ctx->g, ctx->m0, fi, fo, U, nullptr, nrhs, nullptr, ctx->stream)))
+            return rc;
+    }
+    if ((rc = launch_from_internal(prec, ctx->work_out.as<char>(), out, V, nrhs, ctx->stream))) return rc;
+    DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return DW_OK;
+}
+
+int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int nmr, dw_prec storage, int nrhs) {
+    if (!ctx || !v || !z) return fail(DW_EINVAL, "null argument");
+    if (check_prec(storage)) return DW_EINVAL;
+    if (nrhs < 1 || nrhs > DW_MAX_RHS) return fail(DW_EINVAL, "nrhs out of range");
+    if (ncycles < 1 || nmr < 1) return fail(DW_EINVAL, "ncycles and nmr must be >= 1");
+    const long long V = ctx->g.V;
+    const long long fb = spinor_bytes(storage, V);
+    int rc;
+    const char* U;
+    if ((rc = gauge_for(ctx, storage, &U))) return rc;
+    if ((rc = ctx->work_in.ensure((size_t)nrhs * fb))) return rc;
+    if ((rc = ctx->work_out.ensure((size_t)nrhs * fb))) return rc;
+    if ((rc = launch_to_internal(storage, v, ctx->work_in.as<char>(), V, nrhs, ctx->stream))) return rc;
+    FieldRef fv{ctx->work_in.as<char>(), fb, 0, 0}, fx{ctx->work_out.as<char>(), fb, 0, 0};
+    for (int cyc = 0; cyc < ncycles; ++cyc)
+        for (int colour = 0; colour < 2; ++colour) {
+            const int mode = (cyc > 0) ? 2 : (colour == 0 ? 0 : 1);
+            ProfScope ps(&ctx->prof, "sap_sweep",
+                         (double)nrhs * 0.5 * (2.0 * fb + (mode == 2 ? fb : 0) + link_bytes(storage, V)));
+            if ((rc = launch_sap_sweep(storage, storage, ctx->g, ctx->m0, fv, fx, U, nullptr, nrhs, colour, nmr, mode,
+                                       ctx->sap_threads[storage], ctx->stream)))
+                return rc;
+        }
+    if ((rc = launch_from_internal(storage, ctx->work_out.as<char>(), z, V, nrhs, ctx->stream))) return rc;
+    DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return DW_OK;
+}
+
+void dw_default_params(dw_solver_params* P) {
+    if (!P) return;
+    std::memset(P, 0, sizeof(*P));
+    P->m = 30;
+    P->k = 10;
+    P->tol = 1e-10;
+    P->max_cycles = 500;
+    P->max_iterations = 0;
+    P->sap_cycles = 5;
+    P->mr_steps = 4;
+    P->sap_prec = DW_F32;
+    P->matvec_prec = DW_F32;
+    P->clean_restart_t = 4.0;
+    P->nrhs = 1;
+    P->host_buffers = 0;
+    P->use_x0 = 0;
+}
+
+int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S) {
+    if (!ctx || !b || !x || !P) return fail(DW_EINVAL, "null argument");
+    if (P->m < 1 || P->m > 63) return fail(DW_EINVAL, "m must be in 1..63");
+    if (P->k < 0 || P->k >= P->m || P->k > 16) return fail(DW_EINVAL, "k must satisfy 0 <= k < m and k <= 16");
+    if (!(P->tol > 0.0)) return fail(DW_EINVAL, "tol must be positive");
+    if (P->max_cycles < 1) return fail(DW_EINVAL, "max_cycles must be >= 1");
+    if (P->sap_cycles < 1 || P->mr_steps < 1) return fail(DW_EINVAL, "sap_cycles and mr_steps must be >= 1");
+    if (check_prec(P->sap_prec)) return DW_EINVAL;
+    if (P->matvec_prec != DW_F64 && P->matvec_prec != DW_F32)
+        return fail(DW_EINVAL, "matvec_prec must be DW_F64 or DW_F32");
+    if (P->nrhs < 1 || P->nrhs > DW_MAX_RHS) return fail(DW_EINVAL, "nrhs out of range");
+    if (!(P->clean_restart_t > 1.0)) return fail(DW_EINVAL, "clean_restart_t must be > 1");
+    return solve(ctx, b, x, P, S);
+}
+
+int dw_profile(dw_ctx* ctx, int enable) {
+    if (!ctx) return fail(DW_EINVAL, "null context");
+    ctx->prof.on = enable != 0;
+    return DW_OK;
+}
+
+int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset) {
+    if (!ctx || !n) return fail(DW_EINVAL, "null argument");
+    ctx->prof.drain();
+    int cnt = 0;
+    for (auto& e : ctx->prof.k) {
+        if (out && cnt < max) {
+            std::memset(&out[cnt], 0, sizeof(dw_kernel_stat));
+            std::strncpy(out[cnt].name, e.name.c_str(), sizeof(out[cnt].name) - 1);
+            out[cnt].launches = e.launches;
+            out[cnt].total_ms = e.total_ms;
+            out[cnt].bytes = e.bytes;
+        }
+        ++cnt;
+    }
+    *n = cnt;
+    if (reset) ctx->prof.reset();
+    return DW_OK;
+}
+
+// ---- host-only small dense routines (include/dwsolve_dense.h) --------------
+int dw_dense_eig(int n, const double* A, double* lam, double* vecs) {
+    if (n < 1 || !A || !lam || !vecs) return fail(DW_EINVAL, "bad argument");
+    return eig(n, reinterpret_cast<const zd*>(A), reinterpret_cast<zd*>(lam), reinterpret_cast<zd*>(vecs)) == 0
+               ? DW_OK
+               : fail(DW_EBREAKDOWN, "eigenvalue iteration did not converge");
+}
+
+int dw_dense_qr(int rows, int cols, const double* G, double* Q, double* R) {
+    if (rows < cols || cols < 1 || !G || !Q) return fail(DW_EINVAL, "bad argument");
+    return qr_positive(rows, cols, reinterpret_cast<const zd*>(G), reinterpret_cast<zd*>(Q),
+                       reinterpret_cast<zd*>(R)) == 0
+               ? DW_OK
+               : fail(DW_EBREAKDOWN, "rank-deficient matrix");
+}
+
+int dw_dense_lstsq(int rows, int cols, int dense_rows, const double* H, const double* c, double* eta,
+                   double* residual) {
+    if (rows < cols + 1 || cols < 1 || !H || !c || !eta || !residual) return fail(DW_EINVAL, "bad argument");
+    GivensLS ls;
+    ls.reset(reinterpret_cast<const zd*>(c), rows, cols);
+    std::vector<zd> col(rows);
+    const zd* Hz = reinterpret_cast<const zd*>(H);
+    for (int j = 0; j < cols; ++j) {
+        for (int i = 0; i < rows; ++i) col[i] = Hz[(size_t)i * cols + j];
+        const int nz = (j < dense_rows - 1) ? dense_rows : j + 2;
+        residual[j] = ls.add_column(col.data(), nz < rows ? nz : rows);
+    }
+    ls.solve(reinterpret_cast<zd*>(eta));
+    return DW_OK;
+}
+
+int dw_dense_solve(int n, const double* A, double* b) {
+    if (n < 1 || !A || !b) return fail(DW_EINVAL, "bad argument");
+    const zd* Az = reinterpret_cast<const zd*>(A);
+    std::vector<zd> M(Az, Az + (size_t)n * n);
+    return lu_solve(n, M, reinterpret_cast<zd*>(b)) == 0 ? DW_OK : fail(DW_EBREAKDOWN, "singular matrix");
+}
+
+}  // extern "C"

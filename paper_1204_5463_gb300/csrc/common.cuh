@@ -1,0 +1,336 @@
+// Device-side building blocks shared by the CUDA kernels of the library:
+// complex arithmetic, storage formats of spinor and link fields, lattice
+// geometry, and the spin-projected hopping term of the Wilson-Dirac operator
+// (Sec. 2, Eq. "Dw").
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwk {
+
+// ---------------------------------------------------------------------------
+// complex numbers
+// ---------------------------------------------------------------------------
+template <class R>
+struct cx {
+    R re, im;
+};
+
+template <class R>
+__device__ __forceinline__ cx<R> mk(R a, R b) {
+    cx<R> z;
+    z.re = a;
+    z.im = b;
+    return z;
+}
+template <class R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <class R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk(s * a.re, s * a.im); }
+// conj(a) * b
+template <class R>
+__device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+    return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// i * a and -i * a
+template <class R>
+__device__ __forceinline__ cx<R> ti(cx<R> a) { return mk(-a.im, a.re); }
+template <class R>
+__device__ __forceinline__ cx<R> tmi(cx<R> a) { return mk(a.im, -a.re); }
+template <class R>
+__device__ __forceinline__ cx<R> czero() { return mk<R>(R(0), R(0)); }
+
+// ---------------------------------------------------------------------------
+// lattice geometry
+// ---------------------------------------------------------------------------
+struct Geom {
+    int d[4];      // lattice extents d1..d4 (site index n1 + d1*(n2 + d2*(n3 + d3*n4)))
+    int b[4];      // domain block extents
+    int nb[4];     // domains per direction
+    long long V;   // number of sites
+    int B;         // sites per domain
+    int ndom;      // number of domains
+};
+
+__device__ __forceinline__ void site_coords(const Geom& g, long long s, int x[4]) {
+    long long t = s;
+    x[0] = (int)(t % g.d[0]);
+    t /= g.d[0];
+    x[1] = (int)(t % g.d[1]);
+    t /= g.d[1];
+    x[2] = (int)(t % g.d[2]);
+    x[3] = (int)(t / g.d[2]);
+}
+
+__device__ __forceinline__ long long site_index(const Geom& g, const int x[4]) {
+    return x[0] + (long long)g.d[0] * (x[1] + (long long)g.d[1] * (x[2] + (long long)g.d[2] * x[3]));
+}
+
+// neighbour of site s (coords x) in direction mu, sign +1/-1, periodic
+__device__ __forceinline__ long long neighbour(const Geom& g, long long s, const int x[4], int mu, int sign) {
+    long long stride = 1;
+    for (int j = 0; j < mu; ++j) stride *= g.d[j];
+    if (sign > 0) return (x[mu] == g.d[mu] - 1) ? s - (long long)(g.d[mu] - 1) * stride : s + stride;
+    return (x[mu] == 0) ? s + (long long)(g.d[mu] - 1) * stride : s - stride;
+}
+
+// ---------------------------------------------------------------------------
+// storage formats
+//
+// spinor fields, component-major with the site index fastest:
+//   S64 : double2 [12][V]                       192 B/site
+//   S32 : float4  [6][V]  (two complex each)     96 B/site
+//   S16 : uint4   [3][V]  (eight halves each) + float scale[V]   52 B/site
+//   SB16: as S16 with bfloat16                                   52 B/site
+// For S16/SB16 each site stores psi/s with s = max |real component| of the
+// site (s = 1 for a zero site), so every stored value lies in [-1, 1].
+//
+// link fields U[mu][row][col], component-major with the site index fastest:
+//   L64: double2 [4][9][V], L32: float2, L16: half2, LB16: bfloat162
+// ---------------------------------------------------------------------------
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+
+__host__ __device__ inline long long spinor_bytes(int prec, long long V) {
+    return prec == P64 ? 192 * V : prec == P32 ? 96 * V : 52 * V;
+}
+__host__ __device__ inline long long link_bytes(int prec, long long V) {
+    return prec == P64 ? 576 * V : prec == P32 ? 288 * V : 144 * V;
+}
+
+template <int P>
+struct real_of {
+    typedef float type;
+};
+template <>
+struct real_of<P64> {
+    typedef double type;
+};
+
+__device__ __forceinline__ float2 h2_to_f2(uint32_t u, int bf) {
+    if (bf) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+        return __bfloat1622float2(h);
+    }
+    __half2 h = *reinterpret_cast<__half2*>(&u);
+    return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2_to_h2(float a, float b, int bf) {
+    uint32_t u;
+    if (bf) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        u = *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        u = *reinterpret_cast<uint32_t*>(&h);
+    }
+    return u;
+}
+
+template <class T, bool G>
+__device__ __forceinline__ T ld(const T* p) {
+    if constexpr (G)
+        return __ldg(p);
+    else
+        return *p;
+}
+
+// load the 12 complex components of site s into compute type C
+// (G = true: global memory through the read-only path; false: shared memory)
+template <int P, class C, bool G = true>
+__device__ __forceinline__ void load_spinor(const char* base, long long V, long long s, cx<C> out[12]) {
+    if constexpr (P == P64) {
+        const double2* p = reinterpret_cast<const double2*>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 v = ld<double2, G>(&p[c * V + s]);
+            out[c] = mk<C>((C)v.x, (C)v.y);
+        }
+    } else if constexpr (P == P32) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            float4 v = ld<float4, G>(&p[q * V + s]);
+            out[2 * q] = mk<C>((C)v.x, (C)v.y);
+            out[2 * q + 1] = mk<C>((C)v.z, (C)v.w);
+        }
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(base);
+        const float sc = ld<float, G>(reinterpret_cast<const float*>(p + 3 * V) + s);
+        constexpr int bf = (P == PB16);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            uint4 v = ld<uint4, G>(&p[q * V + s]);
+            float2 a = h2_to_f2(v.x, bf), b = h2_to_f2(v.y, bf), c = h2_to_f2(v.z, bf), d = h2_to_f2(v.w, bf);
+            out[4 * q + 0] = mk<C>((C)(sc * a.x), (C)(sc * a.y));
+            out[4 * q + 1] = mk<C>((C)(sc * b.x), (C)(sc * b.y));
+            out[4 * q + 2] = mk<C>((C)(sc * c.x), (C)(sc * c.y));
+            out[4 * q + 3] = mk<C>((C)(sc * d.x), (C)(sc * d.y));
+        }
+    }
+}
+
+template <int P, class C>
+__device__ __forceinline__ void store_spinor(char* base, long long V, long long s, const cx<C> in[12]) {
+    if constexpr (P == P64) {
+        double2* p = reinterpret_cast<double2*>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[c * V + s] = make_double2((double)in[c].re, (double)in[c].im);
+    } else if constexpr (P == P32) {
+        float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            p[q * V + s] = make_float4((float)in[2 * q].re, (float)in[2 * q].im, (float)in[2 * q + 1].re,
+                                       (float)in[2 * q + 1].im);
+    } else {
+        uint4* p = reinterpret_cast<uint4*>(base);
+        float mx = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) mx = fmaxf(mx, fmaxf(fabsf((float)in[c].re), fabsf((float)in[c].im)));
+        const float sc = (mx > 0.f) ? mx : 1.f;
+        const float inv = 1.f / sc;
+        constexpr int bf = (P == PB16);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            uint4 v;
+            v.x = f2_to_h2((float)in[4 * q + 0].re * inv, (float)in[4 * q + 0].im * inv, bf);
+            v.y = f2_to_h2((float)in[4 * q + 1].re * inv, (float)in[4 * q + 1].im * inv, bf);
+            v.z = f2_to_h2((float)in[4 * q + 2].re * inv, (float)in[4 * q + 2].im * inv, bf);
+            v.w = f2_to_h2((float)in[4 * q + 3].re * inv, (float)in[4 * q + 3].im * inv, bf);
+            p[q * V + s] = v;
+        }
+        reinterpret_cast<float*>(p + 3 * V)[s] = sc;
+    }
+}
+
+// link U_{s,mu} (3x3, row-major) in compute type C
+template <int P, class C, bool G = true>
+__device__ __forceinline__ void load_link(const char* base, long long V, int mu, long long s, cx<C> u[9]) {
+    if constexpr (P == P64) {
+        const double2* p = reinterpret_cast<const double2*>(base) + (long long)mu * 9 * V;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            double2 v = ld<double2, G>(&p[c * V + s]);
+            u[c] = mk<C>((C)v.x, (C)v.y);
+        }
+    } else if constexpr (P == P32) {
+        const float2* p = reinterpret_cast<const float2*>(base) + (long long)mu * 9 * V;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            float2 v = ld<float2, G>(&p[c * V + s]);
+            u[c] = mk<C>((C)v.x, (C)v.y);
+        }
+    } else {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(base) + (long long)mu * 9 * V;
+        constexpr int bf = (P == PB16);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            float2 v = h2_to_f2(ld<uint32_t, G>(&p[c * V + s]), bf);
+            u[c] = mk<C>((C)v.x, (C)v.y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hopping term
+//
+// Chiral basis: gamma_mu = [[0, A_mu], [A_mu^dagger, 0]] with
+//   A_1 = -i sigma_1, A_2 = -i sigma_2, A_3 = -i sigma_3, A_4 = 1.
+// (1 +- gamma_mu) has rank two: its upper two spin rows h = psi_u +- A_mu psi_l
+// determine the lower two rows +- A_mu^dagger h, so one hop multiplies only
+// two colour vectors by the link.
+//
+// hop<MU, SIGN>(psi, U, acc): acc += (1 + SIGN gamma_MU) W psi with W = U for
+// SIGN = +1 and W = U^dagger for SIGN = -1.
+// ---------------------------------------------------------------------------
+template <class C, bool DAG>
+__device__ __forceinline__ void su3_mul(const cx<C> u[9], const cx<C> h[3], cx<C> k[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<C> acc;
+        if (!DAG) {
+            acc = u[3 * a] * h[0];
+            acc = acc + u[3 * a + 1] * h[1];
+            acc = acc + u[3 * a + 2] * h[2];
+        } else {
+            acc = cmulc(u[a], h[0]);
+            acc = acc + cmulc(u[3 + a], h[1]);
+            acc = acc + cmulc(u[6 + a], h[2]);
+        }
+        k[a] = acc;
+    }
+}
+
+template <int MU, int SIGN, class C>
+__device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C> acc[12]) {
+    cx<C> h0[3], h1[3], k0[3], k1[3];
+    const C s = (C)SIGN;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<C> p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
+        if constexpr (MU == 0) {  // h0 = p0 - s i p3, h1 = p1 - s i p2
+            h0[c] = p0 - s * ti(p3);
+            h1[c] = p1 - s * ti(p2);
+        } else if constexpr (MU == 1) {  // h0 = p0 - s p3, h1 = p1 + s p2
+            h0[c] = p0 - s * p3;
+            h1[c] = p1 + s * p2;
+        } else if constexpr (MU == 2) {  // h0 = p0 - s i p2, h1 = p1 + s i p3
+            h0[c] = p0 - s * ti(p2);
+            h1[c] = p1 + s * ti(p3);
+        } else {  // h0 = p0 + s p2, h1 = p1 + s p3
+            h0[c] = p0 + s * p2;
+            h1[c] = p1 + s * p3;
+        }
+    }
+    su3_mul<C, (SIGN < 0)>(u, h0, k0);
+    su3_mul<C, (SIGN < 0)>(u, h1, k1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = acc[c] + k0[c];
+        acc[3 + c] = acc[3 + c] + k1[c];
+        if constexpr (MU == 0) {  // lower = s i (k1, k0)
+            acc[6 + c] = acc[6 + c] + s * ti(k1[c]);
+            acc[9 + c] = acc[9 + c] + s * ti(k0[c]);
+        } else if constexpr (MU == 1) {  // lower = s (k1, -k0)
+            acc[6 + c] = acc[6 + c] + s * k1[c];
+            acc[9 + c] = acc[9 + c] - s * k0[c];
+        } else if constexpr (MU == 2) {  // lower = s i (k0, -k1)
+            acc[6 + c] = acc[6 + c] + s * ti(k0[c]);
+            acc[9 + c] = acc[9 + c] - s * ti(k1[c]);
+        } else {  // lower = s (k0, k1)
+            acc[6 + c] = acc[6 + c] + s * k0[c];
+            acc[9 + c] = acc[9 + c] + s * k1[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-rhs field addressing for batched launches
+//
+// A FieldRef names one spinor field per right-hand side r:
+//   base + r * rhs_stride + (col(r) + col_off) * col_stride
+// where col(r) = jtab[r] when a column table is given (Krylov bases), else 0.
+// A right-hand side with jtab[r] < 0 is inactive for the launch.
+// ---------------------------------------------------------------------------
+struct FieldRef {
+    char* base;
+    long long rhs_stride;
+    long long col_stride;
+    int col_off;
+};
+
+__device__ __forceinline__ char* field_ptr(const FieldRef& f, const int* jtab, int r) {
+    const int j = jtab ? jtab[r] : 0;
+    return f.base + (long long)r * f.rhs_stride + (long long)(j + f.col_off) * f.col_stride;
+}
+__device__ __forceinline__ bool rhs_active(const int* jtab, int r) { return jtab == nullptr || jtab[r] >= 0; }
+
+}  // namespace dwk

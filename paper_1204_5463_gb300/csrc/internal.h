@@ -1,0 +1,158 @@
+// Host-side internals of the library: the context object and the launchers
+// of the CUDA kernels (declared here, defined in the .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/dwsolve.h"
+#include "common.cuh"
+
+namespace dwk {
+
+typedef std::complex<double> zd;
+
+// thread-local error message behind dw_last_error()
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define DW_CUDA_TRY(expr)                                                                       \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess)                                                                  \
+            return ::dwk::fail(DW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));   \
+    } while (0)
+
+// A device allocation owned by the library (grown on demand, freed with the owner).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t n);
+    void release();
+    template <class T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+    ~DevBuf() { release(); }
+};
+
+// Per-kernel-class timing, collected with CUDA events on the library stream
+// while profiling is switched on.
+struct KernelProfile {
+    std::string name;
+    long long launches = 0;
+    double total_ms = 0.0;
+    double bytes = 0.0;  // algorithmic bytes summed over launches
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<double> pending_bytes;
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<KernelProfile> k;
+    cudaStream_t stream = nullptr;
+    int begin(const char* name, double bytes, cudaEvent_t* start_out, int* idx);
+    void end(int idx, cudaEvent_t start);
+    void drain();  // turn pending event pairs into totals (synchronises)
+    void reset();
+    ~Profiler();
+};
+
+// RAII helper: times the launches issued in its scope as one entry.
+struct ProfScope {
+    Profiler* p;
+    int idx = -1;
+    cudaEvent_t start = nullptr;
+    ProfScope(Profiler* prof, const char* name, double bytes) : p(prof) {
+        if (p && p->on) p->begin(name, bytes, &start, &idx);
+    }
+    ~ProfScope() {
+        if (p && p->on && idx >= 0) p->end(idx, start);
+    }
+};
+
+struct Workspace;                    // Krylov workspace of the solver (solver.cpp)
+void release_workspace(Workspace* w);
+
+}  // namespace dwk
+
+struct dw_ctx {
+    dwk::Geom g;
+    double m0 = 0.0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool have_gauge = false;
+    dwk::DevBuf U[4];           // gauge field per storage precision (P64, P32, P16, PB16)
+    bool U_ready[4] = {false, false, false, false};
+    dwk::DevBuf work_in, work_out, work_aux;  // conversions in dw_apply / sap_precondition
+    dwk::Profiler prof;
+    std::vector<int> sap_threads;  // tuned launch shape per precision (0 = default)
+    dwk::Workspace* ws = nullptr;  // solver workspace, kept between solves
+};
+
+namespace dwk {
+
+// gauge field in the requested storage precision (converted from FP64 on first use)
+int gauge_for(dw_ctx* ctx, int prec, const char** out);
+
+// ----- dw.cu ---------------------------------------------------------------
+int launch_to_internal(int prec, const double* canon, char* out, long long V, int nrhs, cudaStream_t st);
+int launch_from_internal(int prec, const char* in, double* canon, long long V, int nrhs, cudaStream_t st);
+int launch_gauge_convert(int prec, const double* Ucanon, char* out, long long V, cudaStream_t st);
+int launch_link_convert(int prec, const char* U64, char* out, long long V, cudaStream_t st);
+// out = D in  (sub == nullptr)   or   out = sub - D in  (sub: FP64 field, PO must be P64)
+int launch_dw(int pin, int pout, int plink, const Geom& g, double m0, FieldRef in, FieldRef out, const char* U,
+              const int* jtab, int nrhs, const FieldRef* sub, cudaStream_t st);
+
+// ----- sap.cu --------------------------------------------------------------
+// One colour half-sweep of SAP (Algorithm 2) on every domain of `colour`:
+// r = v - D x (full operator), nmr MR steps on D^l y = r, x += y.
+// mode 0: x == 0 everywhere (r = v, x = y); 1: x == 0 on this colour; 2: general.
+int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
+                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st);
+int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads);
+
+// ----- blas.cu -------------------------------------------------------------
+// FP64 flat vectors of n complex numbers (double2).
+struct VecRef {
+    double2* base;
+    long long rhs_stride;  // in double2
+    long long col_stride;  // in double2
+    int col_off;
+};
+// out[r][i] = <V_i, w>  (i < nv[r]),  out[r][nvmax] = ||w||^2 ; nv from jtab (nv = jtab[r] + nv_off)
+int launch_multidot(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
+                    double2* partial, int nblk, double2* out, cudaStream_t st);
+// w -= sum_i coef[r][i] V_i (i < nv[r]);  out_norm2[r] = ||w||^2 after the update
+int launch_multiaxpy(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs, const double2* coef,
+                     int coef_ld, double2* partial, int nblk, double* out_norm2, cudaStream_t st);
+// dst = w * (1 / sqrt(norm2[r])) and optionally a copy in spinor storage precision
+int launch_normalize(VecRef w, VecRef dst, long long n, const int* jtab, int nrhs, const double* norm2,
+                     cudaStream_t st);
+// in place, per site row: X_c = sum_i X_i Q[r][i][c]  (c < kout, i < nin), X in precision prec
+// (scaled FP16/BF16 storage goes through `scratch`, nrhs * kout columns, and is copied back)
+int launch_rotate(int prec, char* X, long long rhs_stride, long long col_stride, long long V, int nrhs,
+                  const int* active, int nin, int kout, const double2* Q, int qld, char* scratch,
+                  cudaStream_t st);
+// x[r] += sum_i Z_i eta[r][i]  (i < nz[r]), Z in precision prec, x FP64 internal;
+// z_rs, z_cs, x_rs in bytes
+int launch_xupdate(int prec, const char* Z, long long z_rs, long long z_cs, double2* x, long long x_rs, long long V,
+                   int nrhs, const int* nz, const double2* eta, int eta_ld, cudaStream_t st);
+// out[r] = ||a[r]||^2 for FP64 internal fields
+int launch_norm2(const double2* a, long long rs, long long n, int nrhs, double2* partial, int nblk, double* out,
+                 cudaStream_t st);
+// copy FP64 field to another precision (spinor storage) for a set of rhs
+int launch_convert(int pin, int pout, FieldRef in, FieldRef out, long long V, const int* jtab, int nrhs,
+                   cudaStream_t st);
+// dst = a * src (FP64 fields), per rhs scalar (a: device array, or nullptr with scalar s)
+int launch_scale(const double2* src, double2* dst, long long rs, long long n, int nrhs, const double* a,
+                 cudaStream_t st);
+int launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+int blas_nblk(long long n);
+
+// ----- solver.cpp ----------------------------------------------------------
+int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S);
+
+}  // namespace dwk

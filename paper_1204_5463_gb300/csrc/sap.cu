@@ -1,0 +1,287 @@
+// One colour half-sweep of the Schwarz alternating procedure (Sec. 2,
+// Algorithm 2) with inexact minimal-residual domain solves (Sec. 3).
+//
+// One CTA owns one domain L^l of the swept colour (and one right-hand side);
+// one thread owns one site of the domain. The CTA
+//   1. stages the domain's own links U_{n,mu} (n in L^l) in shared memory,
+//   2. computes r^l = (v - D x)^l with the full operator (neighbour values of
+//      x come from the opposite colour, read through L2),
+//   3. runs nmr MR steps on D^l y = r^l entirely out of shared memory:
+//        p = D^l rho;  alpha = <p,rho>/<p,p>;  y += alpha rho;  rho -= alpha p
+//      (D^l keeps only hops whose both ends lie in L^l, Eq. "Dw_local"; the
+//      inner products are CTA-wide warp-shuffle reductions),
+//   4. writes x^l + y^l back.
+// Domains of one colour never couple (even domain count per direction), so
+// all CTAs of a launch are independent and the launch order is irrelevant.
+#include "internal.h"
+
+namespace dwk {
+
+namespace {
+
+template <int PL>
+struct link_word {
+    typedef uint32_t type;
+};
+template <>
+struct link_word<P64> {
+    typedef double2 type;
+};
+template <>
+struct link_word<P32> {
+    typedef float2 type;
+};
+
+template <class C>
+__device__ __forceinline__ void block_sum3(C& a, C& b, C& c, C* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[3 * w] = a;
+        red[3 * w + 1] = b;
+        red[3 * w + 2] = c;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    C sa = 0, sb = 0, sc = 0;
+    for (int i = 0; i < nw; ++i) {
+        sa += red[3 * i];
+        sb += red[3 * i + 1];
+        sc += red[3 * i + 2];
+    }
+    a = sa;
+    b = sb;
+    c = sc;
+}
+
+template <int PS, int PL, class C, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1) sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref,
+                                                         const char* __restrict__ U, const int* jtab, int nrhs,
+                                                         int colour, int nmr, int mode) {
+    typedef typename link_word<PL>::type LW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x;
+    C* rho_sh = reinterpret_cast<C*>(smem);                                   // [24][T]
+    LW* link_sh = reinterpret_cast<LW*>(smem + sizeof(C) * 24 * T);          // [4][9][T]
+    C* red = reinterpret_cast<C*>(smem + sizeof(C) * 24 * T + sizeof(LW) * 36 * T);  // [32][3]
+
+    const int r = blockIdx.x % nrhs;
+    const int e = blockIdx.x / nrhs;
+    if (!rhs_active(jtab, r)) return;  // uniform over the CTA
+    const char* vb = field_ptr(vref, jtab, r);
+    char* xb = field_ptr(xref, jtab, r);
+
+    // domain e of this colour: block coordinates D with sum(D) % 2 == colour
+    const int half1 = g.nb[0] >> 1;
+    int D[4];
+    {
+        int t = e / half1;
+        D[1] = t % g.nb[1];
+        t /= g.nb[1];
+        D[2] = t % g.nb[2];
+        D[3] = t / g.nb[2];
+        D[0] = 2 * (e % half1) + ((colour + D[1] + D[2] + D[3]) & 1);
+    }
+    const int tid = threadIdx.x;
+    const bool act = tid < g.B;
+    int lx[4], xg[4];
+    {
+        int q = act ? tid : 0;
+        lx[0] = q % g.b[0];
+        q /= g.b[0];
+        lx[1] = q % g.b[1];
+        q /= g.b[1];
+        lx[2] = q % g.b[2];
+        lx[3] = q / g.b[2];
+    }
+    const int lstride[4] = {1, g.b[0], g.b[0] * g.b[1], g.b[0] * g.b[1] * g.b[2]};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xg[j] = D[j] * g.b[j] + lx[j];
+    const long long s = site_index(g, xg);
+
+    // 1. own links -> shared memory (raw storage words)
+    if (act) {
+        const LW* Ug = reinterpret_cast<const LW*>(U);
+#pragma unroll 4
+        for (int c = 0; c < 36; ++c) link_sh[c * T + tid] = Ug[(long long)c * g.V + s];
+    }
+
+    // 2. residual r = v - D x at this site
+    cx<C> rho[12], y[12];
+    if (act) {
+        load_spinor<PS, C>(vb, g.V, s, rho);
+        if (mode != 0) {
+            cx<C> acc[12], psi[12], u[9];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = czero<C>();
+            const bool own_zero = (mode == 1);
+#define SAP_RES_HOPS(MU)                                                                     \
+    {                                                                                        \
+        const bool in_p = lx[MU] + 1 < g.b[MU];                                              \
+        if (!(own_zero && in_p)) {                                                           \
+            load_spinor<PS, C>(xb, g.V, neighbour(g, s, xg, MU, +1), psi);                   \
+            load_link<PL, C>(U, g.V, MU, s, u);                                              \
+            hop<MU, +1, C>(psi, u, acc);                                                     \
+        }                                                                                    \
+        const bool in_m = lx[MU] >= 1;                                                       \
+        if (!(own_zero && in_m)) {                                                           \
+            const long long sm = neighbour(g, s, xg, MU, -1);                                \
+            load_spinor<PS, C>(xb, g.V, sm, psi);                                            \
+            load_link<PL, C>(U, g.V, MU, sm, u);                                             \
+            hop<MU, -1, C>(psi, u, acc);                                                     \
+        }                                                                                    \
+    }
+            SAP_RES_HOPS(0)
+            SAP_RES_HOPS(1)
+            SAP_RES_HOPS(2)
+            SAP_RES_HOPS(3)
+#undef SAP_RES_HOPS
+            const C half = (C)0.5;
+            if (!own_zero) {
+                load_spinor<PS, C>(xb, g.V, s, psi);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) rho[c] = rho[c] - (diag * psi[c] - half * acc[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) rho[c] = rho[c] + half * acc[c];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) rho[c] = czero<C>();
+    }
+#pragma unroll
+    for (int c = 0; c < 12; ++c) y[c] = czero<C>();
+
+    // 3. MR on D^l y = r^l out of shared memory
+    const char* lsh = reinterpret_cast<const char*>(link_sh);
+    for (int it = 0; it < nmr; ++it) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            rho_sh[(2 * c) * T + tid] = rho[c].re;
+            rho_sh[(2 * c + 1) * T + tid] = rho[c].im;
+        }
+        __syncthreads();
+        cx<C> p[12];
+        C pr_re = 0, pr_im = 0, pp = 0;
+        if (act) {
+            cx<C> acc[12], psi[12], u[9];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = czero<C>();
+#define SAP_LOC_HOPS(MU)                                                                      \
+    {                                                                                         \
+        if (lx[MU] + 1 < g.b[MU]) {                                                           \
+            const int tn = tid + lstride[MU];                                                 \
+            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] =                           \
+                mk<C>(rho_sh[(2 * c) * T + tn], rho_sh[(2 * c + 1) * T + tn]);                \
+            load_link<PL, C, false>(lsh, T, MU, tid, u);                                      \
+            hop<MU, +1, C>(psi, u, acc);                                                      \
+        }                                                                                     \
+        if (lx[MU] >= 1) {                                                                    \
+            const int tn = tid - lstride[MU];                                                 \
+            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] =                           \
+                mk<C>(rho_sh[(2 * c) * T + tn], rho_sh[(2 * c + 1) * T + tn]);                \
+            load_link<PL, C, false>(lsh, T, MU, tn, u);                                       \
+            hop<MU, -1, C>(psi, u, acc);                                                      \
+        }                                                                                     \
+    }
+            SAP_LOC_HOPS(0)
+            SAP_LOC_HOPS(1)
+            SAP_LOC_HOPS(2)
+            SAP_LOC_HOPS(3)
+#undef SAP_LOC_HOPS
+            const C half = (C)0.5;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                p[c] = diag * rho[c] - half * acc[c];
+                const cx<C> t = cmulc(p[c], rho[c]);
+                pr_re += t.re;
+                pr_im += t.im;
+                pp += p[c].re * p[c].re + p[c].im * p[c].im;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) p[c] = czero<C>();
+        }
+        block_sum3(pr_re, pr_im, pp, red);
+        if (pp > (C)0) {
+            const cx<C> alpha = mk<C>(pr_re / pp, pr_im / pp);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                y[c] = y[c] + alpha * rho[c];
+                rho[c] = rho[c] - alpha * p[c];
+            }
+        }
+    }
+    __syncthreads();  // every residual read of x inside the domain precedes the writes below
+
+    // 4. x^l <- x^l + y^l
+    if (act) {
+        if (mode == 2) {
+            cx<C> xo[12];
+            load_spinor<PS, C>(xb, g.V, s, xo);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) y[c] = y[c] + xo[c];
+        }
+        store_spinor<PS, C>(xb, g.V, s, y);
+    }
+}
+
+template <int PS, int PL, class C>
+int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U, const int* jtab, int nrhs,
+                 int colour, int nmr, int mode, int threads, cudaStream_t st) {
+    typedef typename link_word<PL>::type LW;
+    const size_t smem = sizeof(C) * 24 * threads + sizeof(LW) * 36 * threads + sizeof(C) * 3 * 32;
+    static bool attr_set = false;  // benign race: the attribute value is the same for every caller
+    if (!attr_set) {
+        DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 256>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 1024>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_set = true;
+    }
+    const unsigned nb = (unsigned)(g.ndom / 2) * (unsigned)nrhs;
+    if (threads <= 256)
+        sap_sweep_kernel<PS, PL, C, 256><<<nb, threads, smem, st>>>(g, (C)(4.0 + m0), v, x, U, jtab, nrhs, colour,
+                                                                     nmr, mode);
+    else
+        sap_sweep_kernel<PS, PL, C, 1024><<<nb, threads, smem, st>>>(g, (C)(4.0 + m0), v, x, U, jtab, nrhs, colour,
+                                                                      nmr, mode);
+    DW_CUDA_TRY(cudaGetLastError());
+    return DW_OK;
+}
+
+size_t link_word_bytes(int plink) { return plink == P64 ? 16 : plink == P32 ? 8 : 4; }
+
+}  // namespace
+
+int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads) {
+    const size_t c = (pspin == P64) ? 8 : 4;
+    (void)g;
+    return (int)(c * 24 * threads + link_word_bytes(plink) * 36 * threads + c * 3 * 32);
+}
+
+int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
+                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st) {
+    if (threads <= 0) threads = ((g.B + 31) / 32) * 32;
+    if (threads < g.B || threads % 32 != 0 || threads > 1024) return fail(DW_EINVAL, "bad SAP thread count");
+    if (sap_smem_bytes(pspin, plink, g, threads) > 227 * 1024)
+        return fail(DW_EINVAL, "SAP domain does not fit in shared memory at this precision");
+    if (nmr < 1) return fail(DW_EINVAL, "nmr must be >= 1");
+    if (pspin == P64 && plink == P64)
+        return sap_launch_t<P64, P64, double>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+    if (pspin == P32 && plink == P32)
+        return sap_launch_t<P32, P32, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+    if (pspin == P16 && plink == P16)
+        return sap_launch_t<P16, P16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+    if (pspin == PB16 && plink == PB16)
+        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+    return fail(DW_EINVAL, "unsupported SAP precision combination");
+}
+
+}  // namespace dwk
