@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark: SAP-preconditioned FGMRES-DR solves of D x = b on one GB300.
+
+One step = one complete solve (every stage of the path: SAP sweeps, the
+Arnoldi product, Gram-Schmidt, Givens/least squares, deflated restarts and
+the explicit FP64 residual) of the 16^3 x 32 Wilson workload: links
+U = exp(i eps H) with eps = 0.5, bare mass tuned so the smallest |eigenvalue|
+of D is about 1e-2, 4^4 domains, SAP 5 cycles x 4 MR steps, FGMRES-DR m = 30
+k = 10, tol 1e-10, one Gaussian right-hand side. Inputs are resident in HBM
+when the timed region starts (the Krylov working set, > 1 GB, exceeds L2).
+
+Prints one JSON line (rank 0). Under torchrun every rank solves its own
+right-hand side (replicas; no data-path collective) and the timing is the
+maximum over ranks. ``--impl reference`` times the FP64 CPU oracle on this
+host's cores instead, on a bounded sample of the same solve.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D_w HBM GB/s & % roofline; SAP-FGMRES-DR solves/s, p50/p99 latency vs plain"
+WORKLOAD = "wilson_16x16x16x32"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload():
+    import fieldgen as fg
+
+    cfg = dict(fg.lattice_configs()[WORKLOAD])
+    return cfg
+
+
+def sap_flops_per_site(block, nmr):
+    """Algorithmic FP32 flops of one SAP colour sweep per swept site: the full
+    stencil residual (1392) plus nmr MR steps on D^l (165 per in-domain hop,
+    48 diagonal, 336 for the two inner products and two updates)."""
+    hops_in = sum(2.0 * (b - 1) / b for b in block)
+    return 1392.0 + nmr * (165.0 * hops_in + 48.0 + 336.0)
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    e = t.get(name)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1204_5463_gb300", "csrc", e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != e.get("source_sha256_16"):
+        return None
+    return e["bytes_per_launch"] * e.get("scale", 1.0)
+
+
+def oracle_sample(cfg, U, b, n_iter):
+    """Seconds per Arnoldi step of the oracle on this workload (bounded sample)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    res = oracle.solve(U, b, cfg["dims"], cfg["block"], cfg["m0"], cfg["sap_cycles"], cfg["mr_steps"], cfg["m"],
+                       cfg["k"], cfg["tol"], max_iterations=n_iter)
+    dt = time.perf_counter() - t0
+    return dt / max(1, res.iterations), res.iterations
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import fieldgen as fg
+
+    cfg = workload()
+    U = fg.gauge_field(cfg["dims"], cfg["eps"], cfg["seed"])
+    b = fg.gaussian_source(cfg["dims"], 1)
+    iters_per_solve = args.ref_iterations
+    for _ in range(args.warmup):
+        oracle_sample(cfg, U, b, 1)
+    total = 0.0
+    per = []
+    for _ in range(args.steps):
+        t_it, _ = oracle_sample(cfg, U, b, 2)
+        per.append(t_it * iters_per_solve)
+        total += t_it * iters_per_solve
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": cfg["dims"], "block": cfg["block"], "m0": cfg["m0"],
+                   "m": cfg["m"], "k": cfg["k"], "sap": [cfg["sap_cycles"], cfg["mr_steps"]], "tol": cfg["tol"]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"2 Arnoldi steps of the FP64 oracle per step, extrapolated to "
+                                   f"{iters_per_solve} steps per solve (the GPU solve's count)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-iterations", type=int, default=60,
+                    help="Arnoldi steps per solve used to scale the reference sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sap-prec", default="f32")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return rc
+
+    import fieldgen as fg
+    import paper_1204_5463_gb300 as dw
+
+    torch.cuda.set_device(local)
+    cfg = workload()
+    dims, block = cfg["dims"], cfg["block"]
+    V = fg.volume(dims)
+    U = fg.gauge_field(dims, cfg["eps"], cfg["seed"])
+    b = fg.gaussian_source(dims, 1 + rank)
+    stream = torch.cuda.current_stream()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).reshape(-1).copy()).cuda()
+
+    ctx = dw.dw_create(dims, block, cfg["m0"], stream.cuda_stream)
+    Ud = dev(U)
+    dw.dw_set_gauge(ctx, Ud, True)
+    bd = dev(b)
+    xd = torch.zeros_like(bd)
+    P = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                             mr_steps=cfg["mr_steps"], sap_prec=dw.PREC[args.sap_prec], matvec_prec=dw.DW_F32)
+
+    for _ in range(args.warmup):
+        S = dw.fgmresdr_solve(ctx, bd, xd, P)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    dw.dw_profile(ctx, True)
+    dw.dw_profile_read(ctx, reset=True)
+    barrier()
+    if clocks:
+        clocks.start()
+    launches0 = dw.dw_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    lat = []
+    iters = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        S = dw.fgmresdr_solve(ctx, bd, xd, P)
+        lat.append(1e3 * (time.perf_counter() - t0))
+        iters.append(S.iterations)
+        assert S.converged == 1 and S.true_rel_res[0] <= cfg["tol"]
+    ev1.record(stream)
+    barrier()
+    launches = dw.dw_kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    prof = dw.dw_profile_read(ctx, reset=True)
+    dw.dw_profile(ctx, False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = args.steps * world / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the call
+    bh = torch.from_numpy(np.ascontiguousarray(b).view(np.float64).reshape(-1).copy()).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    Ph = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                              mr_steps=cfg["mr_steps"], sap_prec=dw.PREC[args.sap_prec], matvec_prec=dw.DW_F32,
+                              host_buffers=1)
+    dw.fgmresdr_solve(ctx, bh.data_ptr(), xh.data_ptr(), Ph)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        dw.fgmresdr_solve(ctx, bh.data_ptr(), xh.data_ptr(), Ph)
+    barrier()
+    e2e_s = time.perf_counter() - e0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = args.steps * world / e2e_s
+
+    # roofline of the dominant kernel class of the step
+    peaks, peak_src = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k]["total_ms"])
+    d = prof[dom]
+    avg_ms = d["total_ms"] / d["launches"]
+    if dom == "sap_sweep":
+        flops = (V / 2) * sap_flops_per_site(block, cfg["mr_steps"])
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "peak_source": "derived (152 SM x 128 FP32 x 2 x 2.07 GHz)"}
+    else:
+        achieved = (d["bytes"] / d["launches"]) / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_src}
+    tr = kernel_traffic(dom)
+    roof.update({"kernel": dom, "traffic": tr, "launches": d["launches"], "avg_us": 1e3 * avg_ms})
+    shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4) for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 SAP + f32 D z / f64 outer", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(dims), "block": list(block), "m0": cfg["m0"],
+                   "eps": cfg["eps"], "m": cfg["m"], "k": cfg["k"], "sap": [cfg["sap_cycles"], cfg["mr_steps"]],
+                   "sap_prec": args.sap_prec, "tol": cfg["tol"], "nrhs": 1, "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (Krylov basis ~0.8 GB)"},
+        "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)), "min": min(lat)},
+        "iterations": iters,
+        "roofline": roof,
+        "kernel_share": shares,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(bh.numel() * 8),
+                "d2h_bytes_per_step": int(xh.numel() * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        t_it, n = oracle_sample(cfg, U, b, 3)
+        per_solve = t_it * statistics.median(iters)
+        line["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"{n} Arnoldi steps of the FP64 oracle on this workload "
+                                          f"({t_it:.2f} s/step), extrapolated to the GPU solve's "
+                                          f"{int(statistics.median(iters))} steps"}
+    dw.dw_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

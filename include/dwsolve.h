@@ -51,8 +51,12 @@ extern "C" {
  *   DW_F64  FP64 storage, FP64 arithmetic
  *   DW_F32  FP32 storage, FP32 arithmetic
  *   DW_F16  FP16 storage with one FP32 scale per site, FP32 arithmetic
- *   DW_BF16 BF16 storage with one FP32 scale per site, FP32 arithmetic  */
-typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3 } dw_prec;
+ *   DW_BF16 BF16 storage with one FP32 scale per site, FP32 arithmetic
+ *   DW_DF64 double-float: every real is an unevaluated sum hi + lo of two FP32
+ *           numbers (48-bit significand, FP64 footprint); arithmetic on the FP32
+ *           pipes with error-free transformations. Only for the outer Krylov
+ *           vectors of fgmresdr_solve (outer_prec). */
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3, DW_DF64 = 4 } dw_prec;
 
 /* Lattice L = {0 <= n <= d-1} (Sec. 2) and its decomposition into domains
  * L^l of block[] sites each. Requirements: dims[j] >= 2; block[j] >= 1;
@@ -115,6 +119,8 @@ typedef struct {
     int nrhs;               /* right-hand sides solved together, 1..DW_MAX_RHS             */
     int host_buffers;       /* 1: b and x are host pointers (copies inside the call)       */
     int use_x0;             /* 1: x holds the initial guess; 0: x0 = 0                     */
+    dw_prec outer_prec;     /* outer vectors V, x, b, r and their Gram-Schmidt / update
+                               arithmetic: DW_F64 or DW_DF64 (default)                     */
 } dw_solver_params;
 
 typedef struct {
@@ -130,7 +136,7 @@ typedef struct {
 
 /* Defaults: m = 30, k = 10, tol = 1e-10, max_cycles = 500, max_iterations = 0,
  * sap_cycles = 5, mr_steps = 4, sap_prec = DW_F32, matvec_prec = DW_F32,
- * clean_restart_t = 4, nrhs = 1, host_buffers = 0, use_x0 = 0. */
+ * clean_restart_t = 4, nrhs = 1, host_buffers = 0, use_x0 = 0, outer_prec = DW_DF64. */
 void dw_default_params(dw_solver_params* P);
 
 /* Solve D x = b for nrhs right-hand sides with FGMRES-DR (Algorithm 4):
@@ -162,6 +168,10 @@ typedef struct {
 } dw_kernel_stat;
 
 int dw_profile(dw_ctx* ctx, int enable);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts, all threads). */
+long long dw_kernel_launches(void);
 /* Copies up to max entries into out, sets *n; reset != 0 clears the totals. */
 int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset);
 

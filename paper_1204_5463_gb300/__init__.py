@@ -15,9 +15,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdwsolve.so")
 
 DW_OK, DW_EINVAL, DW_ECUDA, DW_ENOMEM, DW_ENOTCONV, DW_EBREAKDOWN, DW_ENONFINITE, DW_ETIMEOUT, DW_ECANCELLED = range(9)
-DW_F64, DW_F32, DW_F16, DW_BF16 = range(4)
+DW_F64, DW_F32, DW_F16, DW_BF16, DW_DF64 = range(5)
 DW_MAX_RHS = 16
-PREC = {"f64": DW_F64, "f32": DW_F32, "f16": DW_F16, "bf16": DW_BF16}
+PREC = {"f64": DW_F64, "f32": DW_F32, "f16": DW_F16, "bf16": DW_BF16, "df64": DW_DF64}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -35,7 +35,8 @@ class dw_solver_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("max_iterations", ctypes.c_int), ("sap_cycles", ctypes.c_int), ("mr_steps", ctypes.c_int),
                 ("sap_prec", ctypes.c_int), ("matvec_prec", ctypes.c_int), ("clean_restart_t", ctypes.c_double),
-                ("nrhs", ctypes.c_int), ("host_buffers", ctypes.c_int), ("use_x0", ctypes.c_int)]
+                ("nrhs", ctypes.c_int), ("host_buffers", ctypes.c_int), ("use_x0", ctypes.c_int),
+                ("outer_prec", ctypes.c_int)]
 
 
 class dw_stats(ctypes.Structure):
@@ -63,6 +64,7 @@ _SIGS = {
     "fgmresdr_solve": ([_P, _P, _P, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_stats)], _I),
     "dw_last_error": ([], ctypes.c_char_p),
     "dw_profile": ([_P, _I], _I),
+    "dw_kernel_launches": ([], ctypes.c_longlong),
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
     "dw_dense_eig": ([_I, _P, _P, _P], _I),
     "dw_dense_qr": ([_I, _I, _P, _P, _P], _I),
@@ -152,6 +154,10 @@ def fgmresdr_solve(ctx, b, x, params: dw_solver_params, allow_notconv: bool = Fa
     _check(rc, "fgmresdr_solve", allow)
     S.status = rc
     return S
+
+
+def dw_kernel_launches() -> int:
+    return int(_lib.dw_kernel_launches())
 
 
 def dw_profile(ctx, enable: bool) -> None:

@@ -1,5 +1,6 @@
 // C ABI of the library (include/dwsolve.h): contexts, the operator, the
 // preconditioner, the solver entry point, error reporting and profiling.
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -10,6 +11,9 @@
 namespace dwk {
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
@@ -118,6 +122,8 @@ using namespace dwk;
 extern "C" {
 
 const char* dw_last_error(void) { return g_err.c_str(); }
+
+long long dw_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out) {
     if (!L || !out) return fail(DW_EINVAL, "null argument");
@@ -257,6 +263,7 @@ void dw_default_params(dw_solver_params* P) {
     P->nrhs = 1;
     P->host_buffers = 0;
     P->use_x0 = 0;
+    P->outer_prec = DW_DF64;
 }
 
 int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S) {
@@ -270,6 +277,7 @@ int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_para
     if (P->matvec_prec != DW_F64 && P->matvec_prec != DW_F32)
         return fail(DW_EINVAL, "matvec_prec must be DW_F64 or DW_F32");
     if (P->nrhs < 1 || P->nrhs > DW_MAX_RHS) return fail(DW_EINVAL, "nrhs out of range");
+    if (P->outer_prec != DW_F64 && P->outer_prec != DW_DF64) return fail(DW_EINVAL, "outer_prec must be DW_F64 or DW_DF64");
     if (!(P->clean_restart_t > 1.0)) return fail(DW_EINVAL, "clean_restart_t must be > 1");
     return solve(ctx, b, x, P, S);
 }

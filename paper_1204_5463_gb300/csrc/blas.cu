@@ -3,8 +3,14 @@
 // the result, normalisation, the basis rotations V_{k+1} = V_{m+1} Q_{k+1},
 // Z_k = Z_m Q_k, and the iterate update x += Z eta.
 //
-// Reductions are deterministic: every CTA writes its partial sums to a fixed
-// slot, and one finishing CTA per right-hand side adds the slots in order.
+// The outer vectors (basis V, iterate x, right-hand side b, residual r) are
+// flat arrays of 16-byte complex elements in one of two formats:
+//   P64 : double2, FP64 arithmetic;
+//   PDF : float4 double-float pairs, double-float arithmetic on the FP32
+//         pipes (same footprint, 48-bit significand) -- the GB300 FP64 rate
+//         would otherwise cap these HBM-bound sweeps far below bandwidth.
+// Reductions are deterministic: every CTA writes its partial sums (FP64) to a
+// fixed slot and one CTA per right-hand side adds the slots in order.
 #include "internal.h"
 
 namespace dwk {
@@ -12,17 +18,9 @@ namespace dwk {
 namespace {
 
 constexpr int kT = 256;      // threads per CTA
-constexpr int kGroup = 8;    // basis vectors handled per sweep of a multi-dot
+constexpr int kGroup = 8;    // basis vectors per sweep of a multi-dot
 constexpr int kRotMax = 17;  // output columns held in registers by a rotation
-
-__device__ __forceinline__ double2 cfma_conj(double2 v, double2 w, double2 acc) {
-    // acc + conj(v) * w
-    acc.x = fma(v.x, w.x, acc.x);
-    acc.x = fma(v.y, w.y, acc.x);
-    acc.y = fma(v.x, w.y, acc.y);
-    acc.y = fma(-v.y, w.x, acc.y);
-    return acc;
-}
+constexpr int kMaxV = 64;    // basis vectors per multi-dot / multi-axpy
 
 __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
@@ -32,11 +30,105 @@ __device__ __forceinline__ double warp_sum(double a) {
 
 __device__ __forceinline__ int rhs_nv(const int* jtab, int r, int off) { return jtab ? jtab[r] + off : off; }
 
-// partial[r][blk][i] = sum over this CTA's elements of conj(V_i) w, i < nv;
-// partial[r][blk][nvmax] = sum |w|^2
+// ---- element access: complex element e of a flat outer vector ---------------
+template <int VP>
+struct Elem;
+
+template <>
+struct Elem<P64> {
+    typedef double2 T;
+    struct C {  // complex accumulator / value
+        double re, im;
+    };
+    static __device__ __forceinline__ C load(const double2* p, long long e) {
+        const double2 v = __ldg(&p[e]);
+        return C{v.x, v.y};
+    }
+    static __device__ __forceinline__ C load_rw(const double2* p, long long e) {
+        const double2 v = p[e];
+        return C{v.x, v.y};
+    }
+    static __device__ __forceinline__ void store(double2* p, long long e, C v) { p[e] = make_double2(v.re, v.im); }
+    static __device__ __forceinline__ C zero() { return C{0.0, 0.0}; }
+    // acc += conj(a) * b
+    static __device__ __forceinline__ void mac_conj(C& acc, C a, C b) {
+        acc.re = fma(a.re, b.re, acc.re);
+        acc.re = fma(a.im, b.im, acc.re);
+        acc.im = fma(a.re, b.im, acc.im);
+        acc.im = fma(-a.im, b.re, acc.im);
+    }
+    // acc += h * a
+    static __device__ __forceinline__ void mac(C& acc, C h, C a) {
+        acc.re = fma(h.re, a.re, acc.re);
+        acc.re = fma(-h.im, a.im, acc.re);
+        acc.im = fma(h.re, a.im, acc.im);
+        acc.im = fma(h.im, a.re, acc.im);
+    }
+    typedef double N;  // |.|^2 accumulator
+    static __device__ __forceinline__ N nzero() { return 0.0; }
+    static __device__ __forceinline__ void norm2_acc(N& s, C a) { s = fma(a.re, a.re, fma(a.im, a.im, s)); }
+    static __device__ __forceinline__ double nfin(N s) { return s; }
+    static __device__ __forceinline__ C fin(C a) { return a; }
+    static __device__ __forceinline__ double2 to_d2(C a) { return make_double2(a.re, a.im); }
+    static __device__ __forceinline__ C from_d2(double2 a) { return C{a.x, a.y}; }
+    static __device__ __forceinline__ C warp_reduce(C a) { return C{warp_sum(a.re), warp_sum(a.im)}; }
+    static __device__ __forceinline__ C scale(C a, double s) { return C{a.re * s, a.im * s}; }
+    static __device__ __forceinline__ cx<float> to_f(C a) { return mk<float>((float)a.re, (float)a.im); }
+};
+
+template <>
+struct Elem<PDF> {
+    typedef float4 T;
+    struct C {
+        df re, im;
+    };
+    static __device__ __forceinline__ C load(const double2* p, long long e) {
+        const float4 v = __ldg(&reinterpret_cast<const float4*>(p)[e]);
+        return C{df{v.x, v.y}, df{v.z, v.w}};
+    }
+    static __device__ __forceinline__ C load_rw(const double2* p, long long e) {
+        const float4 v = reinterpret_cast<const float4*>(p)[e];
+        return C{df{v.x, v.y}, df{v.z, v.w}};
+    }
+    static __device__ __forceinline__ void store(double2* p, long long e, C v) {
+        const df a = df_norm(v.re), b = df_norm(v.im);
+        reinterpret_cast<float4*>(p)[e] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+    static __device__ __forceinline__ C zero() { return C{df{0.f, 0.f}, df{0.f, 0.f}}; }
+    static __device__ __forceinline__ void mac_conj(C& acc, C a, C b) {
+        df_mac(acc.re, a.re, b.re);
+        df_mac(acc.re, a.im, b.im);
+        df_mac(acc.im, a.re, b.im);
+        df_mac(acc.im, df_neg(a.im), b.re);
+    }
+    static __device__ __forceinline__ void mac(C& acc, C h, C a) {
+        df_mac(acc.re, h.re, a.re);
+        df_mac(acc.re, df_neg(h.im), a.im);
+        df_mac(acc.im, h.re, a.im);
+        df_mac(acc.im, h.im, a.re);
+    }
+    typedef df N;
+    static __device__ __forceinline__ N nzero() { return df{0.f, 0.f}; }
+    static __device__ __forceinline__ void norm2_acc(N& s, C a) {
+        df_mac(s, a.re, a.re);
+        df_mac(s, a.im, a.im);
+    }
+    static __device__ __forceinline__ double nfin(N s) { return df_to_double(df_norm(s)); }
+    static __device__ __forceinline__ C fin(C a) { return C{df_norm(a.re), df_norm(a.im)}; }
+    static __device__ __forceinline__ double2 to_d2(C a) { return make_double2(df_to_double(a.re), df_to_double(a.im)); }
+    static __device__ __forceinline__ C from_d2(double2 a) { return C{df_from_double(a.x), df_from_double(a.y)}; }
+    static __device__ __forceinline__ C warp_reduce(C a) { return C{df_warp_sum(df_norm(a.re)), df_warp_sum(df_norm(a.im))}; }
+    static __device__ __forceinline__ C scale(C a, df s) { return C{df_mul(a.re, s), df_mul(a.im, s)}; }
+    static __device__ __forceinline__ cx<float> to_f(C a) { return mk<float>(a.re.hi + a.re.lo, a.im.hi + a.im.lo); }
+};
+
+// ---- multi-dot: partial[r][blk][i] = <V_i, w> (i < nv), [nvmax] = ||w||^2 ---
+template <int VP>
 __global__ void __launch_bounds__(kT) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off,
                                                       int nvmax, double2* partial) {
-    __shared__ double2 sh[64 + 1][kT / 32];
+    typedef Elem<VP> E;
+    typedef typename E::C C;
+    __shared__ double2 sh[kMaxV + 1][kT / 32];
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
     const int nv = rhs_nv(jtab, r, nv_off);
@@ -46,37 +138,37 @@ __global__ void __launch_bounds__(kT) multidot_kernel(VecRef Vb, VecRef w, long 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * kT;
     const long long e0 = (long long)blockIdx.x * kT + threadIdx.x;
-    double wn = 0.0;
+    typename E::N wacc = E::nzero();
     for (int g0 = 0; g0 < nv || g0 == 0; g0 += kGroup) {
-        double2 acc[kGroup];
+        C acc[kGroup];
 #pragma unroll
-        for (int q = 0; q < kGroup; ++q) acc[q] = make_double2(0.0, 0.0);
+        for (int q = 0; q < kGroup; ++q) acc[q] = E::zero();
         const int gn = min(kGroup, nv - g0);
         for (long long e = e0; e < n; e += stride) {
-            const double2 wv = __ldg(&wr[e]);
-            if (g0 == 0) wn = fma(wv.x, wv.x, fma(wv.y, wv.y, wn));
+            const C wv = E::load(wr, e);
+            if (g0 == 0) E::norm2_acc(wacc, wv);
 #pragma unroll
             for (int q = 0; q < kGroup; ++q)
                 if (q < gn) {
                     const double2* vi = Vr + (long long)(g0 + q + Vb.col_off) * Vb.col_stride;
-                    acc[q] = cfma_conj(__ldg(&vi[e]), wv, acc[q]);
+                    E::mac_conj(acc[q], E::load(vi, e), wv);
                 }
         }
 #pragma unroll
         for (int q = 0; q < kGroup; ++q)
             if (q < gn) {
-                const double a = warp_sum(acc[q].x), b = warp_sum(acc[q].y);
-                if (lane == 0) sh[g0 + q][warp] = make_double2(a, b);
+                const C t = E::warp_reduce(acc[q]);
+                if (lane == 0) sh[g0 + q][warp] = E::to_d2(t);
             }
         if (nv == 0) break;
     }
-    wn = warp_sum(wn);
-    if (lane == 0) sh[64][warp] = make_double2(wn, 0.0);
+    const double wn = warp_sum(E::nfin(wacc));
+    if (lane == 0) sh[kMaxV][warp] = make_double2(wn, 0.0);
     __syncthreads();
     const int NP = nvmax + 1;
     double2* out = partial + ((long long)r * gridDim.x + blockIdx.x) * NP;
     for (int i = threadIdx.x; i < NP; i += kT) {
-        const int src = (i == nvmax) ? 64 : i;
+        const int src = (i == nvmax) ? kMaxV : i;
         double2 s = make_double2(0.0, 0.0);
         if (i < nv || i == nvmax)
             for (int q = 0; q < kT / 32; ++q) s.x += sh[src][q].x, s.y += sh[src][q].y;
@@ -101,46 +193,45 @@ __global__ void __launch_bounds__(kT) finalize_kernel(const double2* partial, in
     }
 }
 
-__global__ void __launch_bounds__(kT) finalize_real_kernel(const double2* partial, int nblk, const int* jtab,
+__global__ void __launch_bounds__(32) finalize_real_kernel(const double2* partial, int nblk, const int* jtab,
                                                            double* out) {
     const int r = blockIdx.x;
     if (jtab && jtab[r] < 0) return;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += partial[(long long)r * nblk + b].x;
-        out[r] = s;
-    }
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(long long)r * nblk + b].x;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[r] = s;
 }
 
-// w -= sum_i coef[r][i] V_i ; partial norm of the result
+// ---- w -= sum_i coef[r][i] V_i ; partial ||w||^2 ------------------------------
+template <int VP>
 __global__ void __launch_bounds__(kT) multiaxpy_kernel(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off,
                                                        const double2* coef, int coef_ld, double2* partial) {
-    __shared__ double2 h[64];
+    typedef Elem<VP> E;
+    typedef typename E::C C;
+    __shared__ C h[kMaxV];
     __shared__ double red[kT / 32];
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
     const int nv = rhs_nv(jtab, r, nv_off);
     const int j = jtab ? jtab[r] : 0;
-    for (int i = threadIdx.x; i < nv; i += kT) h[i] = coef[(long long)r * coef_ld + i];
+    for (int i = threadIdx.x; i < nv; i += kT) {
+        const double2 c = coef[(long long)r * coef_ld + i];
+        h[i] = E::from_d2(make_double2(-c.x, -c.y));
+    }
     __syncthreads();
     const double2* Vr = Vb.base + r * Vb.rhs_stride;
     double2* wr = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
     const long long stride = (long long)gridDim.x * kT;
-    double wn = 0.0;
+    typename E::N wacc = E::nzero();
     for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += stride) {
-        double2 acc = wr[e];
-        for (int i = 0; i < nv; ++i) {
-            const double2 v = __ldg(&(Vr + (long long)(i + Vb.col_off) * Vb.col_stride)[e]);
-            const double2 c = h[i];
-            acc.x = fma(-c.x, v.x, acc.x);
-            acc.x = fma(c.y, v.y, acc.x);
-            acc.y = fma(-c.x, v.y, acc.y);
-            acc.y = fma(-c.y, v.x, acc.y);
-        }
-        wr[e] = acc;
-        wn = fma(acc.x, acc.x, fma(acc.y, acc.y, wn));
+        C acc = E::load_rw(wr, e);
+        for (int i = 0; i < nv; ++i) E::mac(acc, h[i], E::load(Vr + (long long)(i + Vb.col_off) * Vb.col_stride, e));
+        acc = E::fin(acc);
+        E::store(wr, e, acc);
+        E::norm2_acc(wacc, acc);
     }
-    wn = warp_sum(wn);
+    const double wn = warp_sum(E::nfin(wacc));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wn;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -150,63 +241,117 @@ __global__ void __launch_bounds__(kT) multiaxpy_kernel(VecRef Vb, VecRef w, long
     }
 }
 
-__global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, long long n, const int* jtab,
-                                                       const double* norm2) {
+// ---- v = w / ||w|| per site, optionally also written in SAP storage ----------
+template <int VP, int PS>
+__global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, long long V, const int* jtab,
+                                                       const double* norm2, FieldRef low) {
+    typedef Elem<VP> E;
+    typedef typename E::C C;
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
+    const long long s = (long long)blockIdx.x * kT + threadIdx.x;
+    if (s >= V) return;
     const int j = jtab ? jtab[r] : 0;
     const double nn = norm2[r];
     const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
     const double2* src = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
     double2* out = dst.base + r * dst.rhs_stride + (long long)(j + dst.col_off) * dst.col_stride;
-    for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
-        const double2 v = src[e];
-        out[e] = make_double2(v.x * inv, v.y * inv);
+    cx<float> f[12];
+    if constexpr (VP == PDF) {
+        const df sc = df_from_double(inv);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            C v = E::scale(E::load_rw(src, c * V + s), sc);
+            E::store(out, c * V + s, v);
+            f[c] = E::to_f(v);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            C v = E::scale(E::load_rw(src, c * V + s), inv);
+            E::store(out, c * V + s, v);
+            f[c] = E::to_f(v);
+        }
     }
+    if constexpr (PS >= 0) store_spinor<PS, float>(field_ptr(low, jtab, r), V, s, f);
 }
 
+template <int VP>
 __global__ void __launch_bounds__(kT) scale_kernel(const double2* src, double2* dst, long long rs, long long n,
                                                    const double* a) {
+    typedef Elem<VP> E;
     const int r = blockIdx.y;
-    const double s = a[r];
     for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
-        const double2 v = src[r * rs + e];
-        dst[r * rs + e] = make_double2(v.x * s, v.y * s);
+        if constexpr (VP == PDF)
+            E::store(dst + r * rs, e, E::scale(E::load_rw(src + r * rs, e), df_from_double(a[r])));
+        else
+            E::store(dst + r * rs, e, E::scale(E::load_rw(src + r * rs, e), a[r]));
     }
 }
 
-// In-place rotation of flat complex columns: X_c = sum_i X_i Q[i][c] (c < kout)
-template <class T2, class R>
-__global__ void __launch_bounds__(kT) rotate_flat_kernel(T2* X, long long rs, long long cs, long long n,
-                                                         const int* active, int nin, int kout, const double2* Q,
-                                                         int qld) {
+// ---- in-place rotation of flat columns: X_c = sum_i X_i Q[i][c] (c < kout) ----
+template <int VP>
+__global__ void __launch_bounds__(kT) rotate_outer_kernel(double2* X, long long rs, long long cs, long long n,
+                                                          const int* active, int nin, int kout, const double2* Q,
+                                                          int qld) {
+    typedef Elem<VP> E;
+    typedef typename E::C C;
+    extern __shared__ __align__(16) unsigned char qsm[];
+    C* q = reinterpret_cast<C*>(qsm);  // [nin][kout]
     const int r = blockIdx.y;
     if (active && !active[r]) return;
-    T2* Xr = X + r * rs;
-    const double2* Qr = Q + (long long)r * qld * qld;  // Q[r][i][c] at Qr[i*qld + c]
+    const double2* Qr = Q + (long long)r * qld * qld;
+    for (int t = threadIdx.x; t < nin * kout; t += kT) q[t] = E::from_d2(Qr[(long long)(t / kout) * qld + t % kout]);
+    __syncthreads();
+    double2* Xr = X + r * rs;
     for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
-        R ar[kRotMax], ai[kRotMax];
+        C acc[kRotMax];
 #pragma unroll
-        for (int c = 0; c < kRotMax; ++c) ar[c] = ai[c] = (R)0;
+        for (int c = 0; c < kRotMax; ++c) acc[c] = E::zero();
         for (int i = 0; i < nin; ++i) {
-            const T2 v = Xr[(long long)i * cs + e];
-            const double2* qrow = Qr + (long long)i * qld;
+            const C v = E::load_rw(Xr + (long long)i * cs, e);
+#pragma unroll
+            for (int c = 0; c < kRotMax; ++c)
+                if (c < kout) E::mac(acc[c], q[i * kout + c], v);
+        }
+#pragma unroll
+        for (int c = 0; c < kRotMax; ++c)
+            if (c < kout) E::store(Xr + (long long)c * cs, e, E::fin(acc[c]));
+    }
+}
+
+// FP32 storage (flat float2 view): X_c = sum_i X_i Q[i][c], in place
+__global__ void __launch_bounds__(kT) rotate_f32_kernel(float2* X, long long rs, long long cs, long long n,
+                                                        const int* active, int nin, int kout, const double2* Q,
+                                                        int qld) {
+    extern __shared__ __align__(16) unsigned char qsm[];
+    float2* q = reinterpret_cast<float2*>(qsm);
+    const int r = blockIdx.y;
+    if (active && !active[r]) return;
+    const double2* Qr = Q + (long long)r * qld * qld;
+    for (int t = threadIdx.x; t < nin * kout; t += kT) {
+        const double2 v = Qr[(long long)(t / kout) * qld + t % kout];
+        q[t] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+    float2* Xr = X + r * rs;
+    for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
+        float ar[kRotMax], ai[kRotMax];
+#pragma unroll
+        for (int c = 0; c < kRotMax; ++c) ar[c] = ai[c] = 0.f;
+        for (int i = 0; i < nin; ++i) {
+            const float2 v = Xr[(long long)i * cs + e];
 #pragma unroll
             for (int c = 0; c < kRotMax; ++c)
                 if (c < kout) {
-                    const double2 q = __ldg(&qrow[c]);
-                    ar[c] += (R)q.x * v.x - (R)q.y * v.y;
-                    ai[c] += (R)q.x * v.y + (R)q.y * v.x;
+                    const float2 qq = q[i * kout + c];
+                    ar[c] = fmaf(qq.x, v.x, fmaf(-qq.y, v.y, ar[c]));
+                    ai[c] = fmaf(qq.x, v.y, fmaf(qq.y, v.x, ai[c]));
                 }
         }
 #pragma unroll
         for (int c = 0; c < kRotMax; ++c)
-            if (c < kout) {
-                T2 o;
-                o.x = ar[c];
-                o.y = ai[c];
-                Xr[(long long)c * cs + e] = o;
-            }
+            if (c < kout) Xr[(long long)c * cs + e] = make_float2(ar[c], ai[c]);
     }
 }
 
@@ -216,11 +361,18 @@ template <int P>
 __global__ void __launch_bounds__(kT) rotate_site_kernel(const char* X, char* Y, long long rs, long long cs,
                                                          long long yrs, long long V, const int* active, int nin,
                                                          int kout, const double2* Q, int qld) {
+    extern __shared__ __align__(16) unsigned char qsm[];
+    float2* q = reinterpret_cast<float2*>(qsm);
     const int r = blockIdx.y;
     if (active && !active[r]) return;
+    const double2* Qr = Q + (long long)r * qld * qld;
+    for (int t = threadIdx.x; t < nin * kout; t += kT) {
+        const double2 v = Qr[(long long)(t / kout) * qld + t % kout];
+        q[t] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
     const long long s = (long long)blockIdx.x * kT + threadIdx.x;
     if (s >= V) return;
-    const double2* Qr = Q + (long long)r * qld * qld;
     for (int c = 0; c < kout; ++c) {
         cx<float> acc[12];
 #pragma unroll
@@ -228,8 +380,7 @@ __global__ void __launch_bounds__(kT) rotate_site_kernel(const char* X, char* Y,
         for (int i = 0; i < nin; ++i) {
             cx<float> v[12];
             load_spinor<P, float>(X + r * rs + i * cs, V, s, v);
-            const double2 q = __ldg(&Qr[(long long)i * qld + c]);
-            const cx<float> qf = mk<float>((float)q.x, (float)q.y);
+            const cx<float> qf = mk<float>(q[i * kout + c].x, q[i * kout + c].y);
 #pragma unroll
             for (int a = 0; a < 12; ++a) acc[a] = acc[a] + qf * v[a];
         }
@@ -237,46 +388,58 @@ __global__ void __launch_bounds__(kT) rotate_site_kernel(const char* X, char* Y,
     }
 }
 
-// x += sum_i Z_i eta_i, one thread per site
-template <int P>
+// ---- x += sum_i Z_i eta_i, one thread per site --------------------------------
+template <int PZ, int VX>
 __global__ void __launch_bounds__(kT) xupdate_kernel(const char* Z, long long z_rs, long long z_cs, double2* x,
                                                      long long x_rs, long long V, const int* nz, const double2* eta,
                                                      int eta_ld) {
+    typedef Elem<VX> E;
+    typedef typename E::C C;
+    __shared__ C et[kMaxV];
     const int r = blockIdx.y;
     const int n = nz[r];
     if (n <= 0) return;
+    for (int i = threadIdx.x; i < n; i += kT) et[i] = E::from_d2(eta[(long long)r * eta_ld + i]);
+    __syncthreads();
     const long long s = (long long)blockIdx.x * kT + threadIdx.x;
     if (s >= V) return;
-    typedef typename real_of<P>::type C;
+    typedef typename real_of<PZ>::type CZ;
     double2* xr = x + r * x_rs;
-    cx<double> acc[12];
+    C acc[12];
 #pragma unroll
-    for (int a = 0; a < 12; ++a) {
-        const double2 t = xr[a * V + s];
-        acc[a] = mk<double>(t.x, t.y);
-    }
+    for (int a = 0; a < 12; ++a) acc[a] = E::load_rw(xr, a * V + s);
     for (int i = 0; i < n; ++i) {
-        cx<C> v[12];
-        load_spinor<P, C>(Z + r * z_rs + i * z_cs, V, s, v);
-        const double2 q = __ldg(&eta[(long long)r * eta_ld + i]);
-        const cx<double> qd = mk<double>(q.x, q.y);
+        cx<CZ> v[12];
+        load_spinor<PZ, CZ>(Z + r * z_rs + i * z_cs, V, s, v);
+        const C h = et[i];
 #pragma unroll
-        for (int a = 0; a < 12; ++a) acc[a] = acc[a] + qd * mk<double>((double)v[a].re, (double)v[a].im);
+        for (int a = 0; a < 12; ++a) {
+            if constexpr (VX == PDF && sizeof(CZ) == 4) {
+                df_mac_f(acc[a].re, h.re, v[a].re);
+                df_mac_f(acc[a].re, df_neg(h.im), v[a].im);
+                df_mac_f(acc[a].im, h.re, v[a].im);
+                df_mac_f(acc[a].im, h.im, v[a].re);
+            } else if constexpr (VX == PDF) {  // FP64 storage of Z: split into double-float pairs
+                E::mac(acc[a], h, typename E::C{df_from_double((double)v[a].re), df_from_double((double)v[a].im)});
+            } else {
+                E::mac(acc[a], h, typename E::C{(double)v[a].re, (double)v[a].im});
+            }
+        }
     }
 #pragma unroll
-    for (int a = 0; a < 12; ++a) xr[a * V + s] = make_double2(acc[a].re, acc[a].im);
+    for (int a = 0; a < 12; ++a) E::store(xr, a * V + s, E::fin(acc[a]));
 }
 
+template <int VP>
 __global__ void __launch_bounds__(kT) norm2_kernel(const double2* a, long long rs, long long n, double2* partial) {
+    typedef Elem<VP> E;
     __shared__ double red[kT / 32];
     const int r = blockIdx.y;
     const double2* ar = a + r * rs;
-    double s = 0.0;
-    for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
-        const double2 v = ar[e];
-        s = fma(v.x, v.x, fma(v.y, v.y, s));
-    }
-    s = warp_sum(s);
+    typename E::N acc = E::nzero();
+    for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT)
+        E::norm2_acc(acc, E::load(ar, e));
+    const double s = warp_sum(E::nfin(acc));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -292,96 +455,142 @@ unsigned grid_for(long long n) {
     return (unsigned)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
+bool outer_ok(int vp) { return vp == P64 || vp == PDF; }
+
 }  // namespace
 
 int blas_nblk(long long n) { return (int)grid_for(n); }
 
-int launch_multidot(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
+int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
                     double2* partial, int nblk, double2* out, cudaStream_t st) {
-    if (nvmax > 64) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
-    multidot_kernel<<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
-    DW_CUDA_TRY(cudaGetLastError());
+    if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
+    if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    if (vp == PDF)
+        multidot_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
+    else
+        multidot_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
+    DW_LAUNCH_CHECK();
     finalize_kernel<<<nrhs, kT, 0, st>>>(partial, nblk, nvmax + 1, jtab, out);
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
-int launch_multiaxpy(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs, const double2* coef,
-                     int coef_ld, double2* partial, int nblk, double* out_norm2, cudaStream_t st) {
-    multiaxpy_kernel<<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
-    DW_CUDA_TRY(cudaGetLastError());
-    finalize_real_kernel<<<nrhs, 32, 0, st>>>(partial, nblk, jtab, out_norm2);
-    DW_CUDA_TRY(cudaGetLastError());
-    return DW_OK;
-}
-
-int launch_normalize(VecRef w, VecRef dst, long long n, const int* jtab, int nrhs, const double* norm2,
+int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs,
+                     const double2* coef, int coef_ld, double2* partial, int nblk, double* out_norm2,
                      cudaStream_t st) {
-    normalize_kernel<<<dim3(grid_for(n), nrhs), kT, 0, st>>>(w, dst, n, jtab, norm2);
-    DW_CUDA_TRY(cudaGetLastError());
+    if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    if (vp == PDF)
+        multiaxpy_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
+    else
+        multiaxpy_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
+    DW_LAUNCH_CHECK();
+    finalize_real_kernel<<<nrhs, 32, 0, st>>>(partial, nblk, jtab, out_norm2);
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
-int launch_scale(const double2* src, double2* dst, long long rs, long long n, int nrhs, const double* a,
+int launch_normalize(int vp, VecRef w, VecRef dst, long long V, const int* jtab, int nrhs, const double* norm2,
+                     int plow, FieldRef low, cudaStream_t st) {
+    if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    dim3 grid((unsigned)((V + kT - 1) / kT), nrhs);
+#define NORM(A, B)                                                                                      \
+    if (vp == A && plow == B) {                                                                         \
+        normalize_kernel<A, B><<<grid, kT, 0, st>>>(w, dst, V, jtab, norm2, low);                       \
+        DW_LAUNCH_CHECK();                                                                              \
+        return DW_OK;                                                                                   \
+    }
+    NORM(P64, -1)
+    NORM(P64, P64)
+    NORM(P64, P32)
+    NORM(P64, P16)
+    NORM(P64, PB16)
+    NORM(PDF, -1)
+    NORM(PDF, P32)
+    NORM(PDF, P16)
+    NORM(PDF, PB16)
+#undef NORM
+    return fail(DW_EINVAL, "unsupported normalisation precision combination");
+}
+
+int launch_scale(int vp, const double2* src, double2* dst, long long rs, long long n, int nrhs, const double* a,
                  cudaStream_t st) {
-    scale_kernel<<<dim3(grid_for(n), nrhs), kT, 0, st>>>(src, dst, rs, n, a);
-    DW_CUDA_TRY(cudaGetLastError());
+    if (vp == PDF)
+        scale_kernel<PDF><<<dim3(grid_for(n), nrhs), kT, 0, st>>>(src, dst, rs, n, a);
+    else
+        scale_kernel<P64><<<dim3(grid_for(n), nrhs), kT, 0, st>>>(src, dst, rs, n, a);
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
 int launch_rotate(int prec, char* X, long long rhs_stride, long long col_stride, long long V, int nrhs,
                   const int* active, int nin, int kout, const double2* Q, int qld, char* scratch,
                   cudaStream_t st) {
-    if (kout > kRotMax && (prec == P64 || prec == P32)) return fail(DW_EINVAL, "deflation dimension too large");
-    if (prec == P64) {
-        const long long n = 12 * V;
-        rotate_flat_kernel<double2, double><<<dim3(grid_for(n), nrhs), kT, 0, st>>>(
-            reinterpret_cast<double2*>(X), rhs_stride / 16, col_stride / 16, n, active, nin, kout, Q, qld);
+    if (kout > kRotMax && prec != P16 && prec != PB16) return fail(DW_EINVAL, "deflation dimension too large");
+    const size_t qsm = (size_t)nin * kout * ((prec == PDF || prec == P64) ? 16 : 8);
+    if (qsm > 48 * 1024) return fail(DW_EINVAL, "rotation matrix too large");
+    const long long n = 12 * V;
+    if (prec == P64 || prec == PDF) {
+        double2* Xd = reinterpret_cast<double2*>(X);
+        if (prec == PDF)
+            rotate_outer_kernel<PDF><<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(Xd, rhs_stride / 16, col_stride / 16,
+                                                                             n, active, nin, kout, Q, qld);
+        else
+            rotate_outer_kernel<P64><<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(Xd, rhs_stride / 16, col_stride / 16,
+                                                                             n, active, nin, kout, Q, qld);
     } else if (prec == P32) {
-        const long long n = 12 * V;
-        rotate_flat_kernel<float2, float><<<dim3(grid_for(n), nrhs), kT, 0, st>>>(
-            reinterpret_cast<float2*>(X), rhs_stride / 8, col_stride / 8, n, active, nin, kout, Q, qld);
+        rotate_f32_kernel<<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(reinterpret_cast<float2*>(X), rhs_stride / 8,
+                                                                    col_stride / 8, n, active, nin, kout, Q, qld);
     } else {
         if (!scratch) return fail(DW_EINVAL, "rotation of scaled storage needs scratch");
         const long long yrs = col_stride * kout;
         dim3 grid((unsigned)((V + kT - 1) / kT), nrhs);
         if (prec == P16)
-            rotate_site_kernel<P16><<<grid, kT, 0, st>>>(X, scratch, rhs_stride, col_stride, yrs, V, active, nin,
-                                                         kout, Q, qld);
+            rotate_site_kernel<P16><<<grid, kT, qsm, st>>>(X, scratch, rhs_stride, col_stride, yrs, V, active, nin,
+                                                           kout, Q, qld);
         else
-            rotate_site_kernel<PB16><<<grid, kT, 0, st>>>(X, scratch, rhs_stride, col_stride, yrs, V, active, nin,
-                                                          kout, Q, qld);
-        DW_CUDA_TRY(cudaGetLastError());
+            rotate_site_kernel<PB16><<<grid, kT, qsm, st>>>(X, scratch, rhs_stride, col_stride, yrs, V, active, nin,
+                                                            kout, Q, qld);
+        DW_LAUNCH_CHECK();
         for (int r = 0; r < nrhs; ++r)
             DW_CUDA_TRY(cudaMemcpyAsync(X + r * rhs_stride, scratch + r * yrs, (size_t)yrs,
                                         cudaMemcpyDeviceToDevice, st));
         return DW_OK;
     }
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
-int launch_xupdate(int prec, const char* Z, long long z_rs, long long z_cs, double2* x, long long x_rs, long long V,
-                   int nrhs, const int* nz, const double2* eta, int eta_ld, cudaStream_t st) {
+int launch_xupdate(int prec, int vx, const char* Z, long long z_rs, long long z_cs, double2* x, long long x_rs,
+                   long long V, int nrhs, const int* nz, const double2* eta, int eta_ld, cudaStream_t st) {
     dim3 grid((unsigned)((V + kT - 1) / kT), nrhs);
     const long long xrs = x_rs / 16;
-    switch (prec) {
-        case P64: xupdate_kernel<P64><<<grid, kT, 0, st>>>(Z, z_rs, z_cs, x, xrs, V, nz, eta, eta_ld); break;
-        case P32: xupdate_kernel<P32><<<grid, kT, 0, st>>>(Z, z_rs, z_cs, x, xrs, V, nz, eta, eta_ld); break;
-        case P16: xupdate_kernel<P16><<<grid, kT, 0, st>>>(Z, z_rs, z_cs, x, xrs, V, nz, eta, eta_ld); break;
-        case PB16: xupdate_kernel<PB16><<<grid, kT, 0, st>>>(Z, z_rs, z_cs, x, xrs, V, nz, eta, eta_ld); break;
-        default: return fail(DW_EINVAL, "bad precision");
+#define XUPD(A, B)                                                                                      \
+    if (prec == A && vx == B) {                                                                         \
+        xupdate_kernel<A, B><<<grid, kT, 0, st>>>(Z, z_rs, z_cs, x, xrs, V, nz, eta, eta_ld);           \
+        DW_LAUNCH_CHECK();                                                                              \
+        return DW_OK;                                                                                   \
     }
-    DW_CUDA_TRY(cudaGetLastError());
-    return DW_OK;
+    XUPD(P64, P64)
+    XUPD(P32, P64)
+    XUPD(P16, P64)
+    XUPD(PB16, P64)
+    XUPD(P64, PDF)
+    XUPD(P32, PDF)
+    XUPD(P16, PDF)
+    XUPD(PB16, PDF)
+#undef XUPD
+    return fail(DW_EINVAL, "unsupported iterate-update precision combination");
 }
 
-int launch_norm2(const double2* a, long long rs, long long n, int nrhs, double2* partial, int nblk, double* out,
-                 cudaStream_t st) {
-    norm2_kernel<<<dim3(nblk, nrhs), kT, 0, st>>>(a, rs, n, partial);
-    DW_CUDA_TRY(cudaGetLastError());
+int launch_norm2(int vp, const double2* a, long long rs, long long n, int nrhs, double2* partial, int nblk,
+                 double* out, cudaStream_t st) {
+    if (vp == PDF)
+        norm2_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(a, rs, n, partial);
+    else
+        norm2_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(a, rs, n, partial);
+    DW_LAUNCH_CHECK();
     finalize_real_kernel<<<nrhs, 32, 0, st>>>(partial, nblk, nullptr, out);
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 

@@ -97,14 +97,88 @@ __device__ __forceinline__ long long neighbour(const Geom& g, long long s, const
 // link fields U[mu][row][col], component-major with the site index fastest:
 //   L64: double2 [4][9][V], L32: float2, L16: half2, LB16: bfloat162
 // ---------------------------------------------------------------------------
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+//   SDF : float4  [12][V]  (re_hi, re_lo, im_hi, im_lo): a double-float pair
+//         per real, value = hi + lo with |lo| <= ulp(hi)/2 (48-bit significand),
+//         192 B/site like S64; its arithmetic runs on the FP32 pipes
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4 };
 
 __host__ __device__ inline long long spinor_bytes(int prec, long long V) {
-    return prec == P64 ? 192 * V : prec == P32 ? 96 * V : 52 * V;
+    return (prec == P64 || prec == PDF) ? 192 * V : prec == P32 ? 96 * V : 52 * V;
 }
 __host__ __device__ inline long long link_bytes(int prec, long long V) {
     return prec == P64 ? 576 * V : prec == P32 ? 288 * V : 144 * V;
 }
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (Dekker 1971 splitting/products, Knuth's TwoSum;
+// products use the FMA form of the exact product error): a value is the
+// unevaluated sum hi + lo of two FP32 numbers.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return df{s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    const float s = a + b;
+    return df{s, b - (s - a)};
+}
+__device__ __forceinline__ df df_norm(df a) { return two_sum(a.hi, a.lo); }
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+// acc += a * b with a lazily normalised accumulator (acc.lo collects the
+// rounding errors; call df_norm before use)
+__device__ __forceinline__ void df_mac(df& acc, df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const df s = two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo += s.lo + e;
+}
+// acc += a * b with b a plain FP32 number
+__device__ __forceinline__ void df_mac_f(df& acc, df a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    const df s = two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo += s.lo + e;
+}
+__device__ __forceinline__ df df_from_double(double x) {
+    const float hi = (float)x;
+    return df{hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+#ifdef __CUDACC__
+// warp-wide sum of a double-float value (every lane gets the sum)
+__device__ __forceinline__ df df_warp_sum(df a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df b;
+        b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        a = df_add(a, b);
+    }
+    return a;
+}
+#endif
 
 template <int P>
 struct real_of {
@@ -112,6 +186,10 @@ struct real_of {
 };
 template <>
 struct real_of<P64> {
+    typedef double type;
+};
+template <>
+struct real_of<PDF> {
     typedef double type;
 };
 
@@ -147,7 +225,17 @@ __device__ __forceinline__ T ld(const T* p) {
 // (G = true: global memory through the read-only path; false: shared memory)
 template <int P, class C, bool G = true>
 __device__ __forceinline__ void load_spinor(const char* base, long long V, long long s, cx<C> out[12]) {
-    if constexpr (P == P64) {
+    if constexpr (P == PDF) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            float4 v = ld<float4, G>(&p[c * V + s]);
+            if constexpr (sizeof(C) == 8)
+                out[c] = mk<C>((C)v.x + (C)v.y, (C)v.z + (C)v.w);
+            else
+                out[c] = mk<C>(v.x + v.y, v.z + v.w);
+        }
+    } else if constexpr (P == P64) {
         const double2* p = reinterpret_cast<const double2*>(base);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
@@ -180,7 +268,18 @@ __device__ __forceinline__ void load_spinor(const char* base, long long V, long 
 
 template <int P, class C>
 __device__ __forceinline__ void store_spinor(char* base, long long V, long long s, const cx<C> in[12]) {
-    if constexpr (P == P64) {
+    if constexpr (P == PDF) {
+        float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            if constexpr (sizeof(C) == 8) {
+                const df a = df_from_double((double)in[c].re), b = df_from_double((double)in[c].im);
+                p[c * V + s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+            } else {
+                p[c * V + s] = make_float4((float)in[c].re, 0.f, (float)in[c].im, 0.f);
+            }
+        }
+    } else if constexpr (P == P64) {
         double2* p = reinterpret_cast<double2*>(base);
 #pragma unroll
         for (int c = 0; c < 12; ++c) p[c * V + s] = make_double2((double)in[c].re, (double)in[c].im);

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kThreads) convert_kernel(FieldRef in, FieldRef
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (s >= V || !rhs_active(jtab, r)) return;
-    typedef typename real_of<(PI == P64 && PO == P64) ? P64 : P32>::type C;
+    // FP64-class precision only when both sides carry it
+    typedef typename real_of<((PI == P64 || PI == PDF) && (PO == P64 || PO == PDF)) ? P64 : P32>::type C;
     cx<C> v[12];
     load_spinor<PI, C>(field_ptr(in, jtab, r), V, s, v);
     store_spinor<PO, C>(field_ptr(out, jtab, r), V, s, v);
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) dw_kernel(Geom g, C diag, FieldRef i
     cx<C> res[12];
     if constexpr (SUB) {
         cx<C> b[12];
-        load_spinor<P64, C>(field_ptr(sub, jtab, r), g.V, s, b);
+        load_spinor<PO, C>(field_ptr(sub, jtab, r), g.V, s, b);
 #pragma unroll
         for (int c = 0; c < 12; ++c) res[c] = b[c] - (diag * psi[c] - half * acc[c]);
     } else {
@@ -147,15 +148,15 @@ int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const c
     const unsigned nb = (unsigned)((g.V + kThreads - 1) / kThreads) * (unsigned)nrhs;
     const C diag = (C)(4.0 + m0);
     if (sub) {
-        if constexpr (PO == P64)
+        if constexpr (PO == P64 || PO == PDF)
             dw_kernel<PI, PO, PL, C, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, *sub);
         else
-            return fail(DW_EINVAL, "residual stencil requires an FP64 output");
+            return fail(DW_EINVAL, "residual stencil requires an FP64-class output");
     } else {
         FieldRef none{};
         dw_kernel<PI, PO, PL, C, false><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, none);
     }
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
@@ -169,9 +170,10 @@ int launch_to_internal(int prec, const double* canon, char* out, long long V, in
         case P32: to_internal_kernel<P32><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
         case P16: to_internal_kernel<P16><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
         case PB16: to_internal_kernel<PB16><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
+        case PDF: to_internal_kernel<PDF><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
         default: return fail(DW_EINVAL, "bad precision");
     }
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
@@ -183,9 +185,10 @@ int launch_from_internal(int prec, const char* in, double* canon, long long V, i
         case P32: from_internal_kernel<P32><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
         case P16: from_internal_kernel<P16><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
         case PB16: from_internal_kernel<PB16><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
+        case PDF: from_internal_kernel<PDF><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
         default: return fail(DW_EINVAL, "bad precision");
     }
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
@@ -198,7 +201,7 @@ int launch_gauge_convert(int prec, const double* U, char* out, long long V, cuda
         case PB16: gauge_convert_kernel<PB16><<<grid, kThreads, 0, st>>>(U, out, V); break;
         default: return fail(DW_EINVAL, "bad precision");
     }
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
@@ -212,7 +215,7 @@ int launch_link_convert(int prec, const char* U64, char* out, long long V, cudaS
         case PB16: link_convert_kernel<PB16><<<nb, kThreads, 0, st>>>(src, out, n); break;
         default: return fail(DW_EINVAL, "bad link precision");
     }
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
@@ -222,7 +225,7 @@ int launch_convert(int pin, int pout, FieldRef in, FieldRef out, long long V, co
 #define CONV(A, B)                                                                            \
     if (pin == A && pout == B) {                                                              \
         convert_kernel<A, B><<<grid, kThreads, 0, st>>>(in, out, V, jtab);                    \
-        DW_CUDA_TRY(cudaGetLastError());                                                      \
+        DW_LAUNCH_CHECK();                                                      \
         return DW_OK;                                                                         \
     }
     CONV(P64, P64)
@@ -232,6 +235,11 @@ int launch_convert(int pin, int pout, FieldRef in, FieldRef out, long long V, co
     CONV(P32, P64)
     CONV(P16, P64)
     CONV(PB16, P64)
+    CONV(PDF, P32)
+    CONV(PDF, P16)
+    CONV(PDF, PB16)
+    CONV(PDF, P64)
+    CONV(P64, PDF)
 #undef CONV
     return fail(DW_EINVAL, "unsupported conversion");
 }
@@ -252,6 +260,14 @@ int launch_dw(int pin, int pout, int plink, const Geom& g, double m0, FieldRef i
     DWC(P32, P64, P64, double)
     DWC(P16, P64, P64, double)
     DWC(PB16, P64, P64, double)
+    DWC(P32, PDF, P32, float)
+    DWC(P16, PDF, P32, float)
+    DWC(PB16, PDF, P32, float)
+    DWC(P32, PDF, P64, double)
+    DWC(P16, PDF, P64, double)
+    DWC(PB16, PDF, P64, double)
+    DWC(PDF, PDF, P64, double)
+    DWC(P64, PDF, P64, double)
 #undef DWC
     return fail(DW_EINVAL, "unsupported stencil precision combination");
 }

@@ -26,6 +26,15 @@ int fail(int code, const std::string& msg);
             return ::dwk::fail(DW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));   \
     } while (0)
 
+// Every kernel launch of the library is followed by DW_LAUNCH_CHECK(): it
+// counts the launch (dw_kernel_launches()) and turns a launch error into DW_ECUDA.
+void count_launch();
+#define DW_LAUNCH_CHECK()          \
+    do {                           \
+        ::dwk::count_launch();     \
+        DW_CUDA_TRY(cudaGetLastError()); \
+    } while (0)
+
 // A device allocation owned by the library (grown on demand, freed with the owner).
 struct DevBuf {
     void* p = nullptr;
@@ -114,39 +123,42 @@ int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v,
 int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads);
 
 // ----- blas.cu -------------------------------------------------------------
-// FP64 flat vectors of n complex numbers (double2).
+// Outer vectors: flat arrays of 16-byte complex elements, format vp = P64
+// (double2) or PDF (double-float float4). Column addressing as for FieldRef,
+// in elements.
 struct VecRef {
     double2* base;
-    long long rhs_stride;  // in double2
-    long long col_stride;  // in double2
+    long long rhs_stride;  // in elements
+    long long col_stride;  // in elements
     int col_off;
 };
-// out[r][i] = <V_i, w>  (i < nv[r]),  out[r][nvmax] = ||w||^2 ; nv from jtab (nv = jtab[r] + nv_off)
-int launch_multidot(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
+// out[r][i] = <V_i, w>  (i < nv[r]),  out[r][nvmax] = ||w||^2 ; nv = jtab[r] + nv_off (or nv_off)
+int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
                     double2* partial, int nblk, double2* out, cudaStream_t st);
 // w -= sum_i coef[r][i] V_i (i < nv[r]);  out_norm2[r] = ||w||^2 after the update
-int launch_multiaxpy(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs, const double2* coef,
-                     int coef_ld, double2* partial, int nblk, double* out_norm2, cudaStream_t st);
-// dst = w * (1 / sqrt(norm2[r])) and optionally a copy in spinor storage precision
-int launch_normalize(VecRef w, VecRef dst, long long n, const int* jtab, int nrhs, const double* norm2,
+int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs,
+                     const double2* coef, int coef_ld, double2* partial, int nblk, double* out_norm2,
                      cudaStream_t st);
-// in place, per site row: X_c = sum_i X_i Q[r][i][c]  (c < kout, i < nin), X in precision prec
+// dst = w / sqrt(norm2[r]) per site; if plow >= 0 also written to `low` in spinor storage plow
+int launch_normalize(int vp, VecRef w, VecRef dst, long long V, const int* jtab, int nrhs, const double* norm2,
+                     int plow, FieldRef low, cudaStream_t st);
+// in place, per element: X_c = sum_i X_i Q[r][i][c]  (c < kout, i < nin), X in precision prec
 // (scaled FP16/BF16 storage goes through `scratch`, nrhs * kout columns, and is copied back)
 int launch_rotate(int prec, char* X, long long rhs_stride, long long col_stride, long long V, int nrhs,
                   const int* active, int nin, int kout, const double2* Q, int qld, char* scratch,
                   cudaStream_t st);
-// x[r] += sum_i Z_i eta[r][i]  (i < nz[r]), Z in precision prec, x FP64 internal;
+// x[r] += sum_i Z_i eta[r][i]  (i < nz[r]), Z in precision prec, x outer format vx;
 // z_rs, z_cs, x_rs in bytes
-int launch_xupdate(int prec, const char* Z, long long z_rs, long long z_cs, double2* x, long long x_rs, long long V,
-                   int nrhs, const int* nz, const double2* eta, int eta_ld, cudaStream_t st);
-// out[r] = ||a[r]||^2 for FP64 internal fields
-int launch_norm2(const double2* a, long long rs, long long n, int nrhs, double2* partial, int nblk, double* out,
-                 cudaStream_t st);
-// copy FP64 field to another precision (spinor storage) for a set of rhs
+int launch_xupdate(int prec, int vx, const char* Z, long long z_rs, long long z_cs, double2* x, long long x_rs,
+                   long long V, int nrhs, const int* nz, const double2* eta, int eta_ld, cudaStream_t st);
+// out[r] = ||a[r]||^2
+int launch_norm2(int vp, const double2* a, long long rs, long long n, int nrhs, double2* partial, int nblk,
+                 double* out, cudaStream_t st);
+// convert a spinor field between storage precisions for a set of rhs
 int launch_convert(int pin, int pout, FieldRef in, FieldRef out, long long V, const int* jtab, int nrhs,
                    cudaStream_t st);
-// dst = a * src (FP64 fields), per rhs scalar (a: device array, or nullptr with scalar s)
-int launch_scale(const double2* src, double2* dst, long long rs, long long n, int nrhs, const double* a,
+// dst = a[r] * src  (outer vectors)
+int launch_scale(int vp, const double2* src, double2* dst, long long rs, long long n, int nrhs, const double* a,
                  cudaStream_t st);
 int launch_zero(void* p, size_t bytes, cudaStream_t st);
 

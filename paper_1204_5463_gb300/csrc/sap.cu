@@ -252,7 +252,7 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
     else
         sap_sweep_kernel<PS, PL, C, 1024><<<nb, threads, smem, st>>>(g, (C)(4.0 + m0), v, x, U, jtab, nrhs, colour,
                                                                       nmr, mode);
-    DW_CUDA_TRY(cudaGetLastError());
+    DW_LAUNCH_CHECK();
     return DW_OK;
 }
 

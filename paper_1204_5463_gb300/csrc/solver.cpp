@@ -45,7 +45,7 @@ struct Solver {
     cudaStream_t st;
     Geom g;
     long long V, n;
-    int nrhs, m, k, sp, mp;
+    int nrhs, m, k, sp, mp, op;  // op: format of the outer vectors (P64 or PDF)
     long long sb;       // bytes of one spinor field in SAP storage
     long long fb;       // bytes of one FP64 internal field
     int NP;             // multi-dot row length (m + 2)
@@ -130,8 +130,9 @@ int Solver::setup() {
     k = P.k;
     sp = (int)P.sap_prec;
     mp = (int)P.matvec_prec;
+    op = (P.outer_prec == DW_DF64) ? PDF : P64;
     sb = spinor_bytes(sp, V);
-    fb = spinor_bytes(P64, V);
+    fb = spinor_bytes(op, V);
     NP = m + 2;
     nblk = blas_nblk(n);
     int rc;
@@ -205,7 +206,7 @@ int Solver::start_plain(int r) {
     int rc;
     {
         ProfScope ps(&ctx->prof, "scale", 2.0 * fb);
-        if ((rc = launch_scale(reinterpret_cast<double2*>(rb) + (long long)r * n,
+        if ((rc = launch_scale(op, reinterpret_cast<double2*>(rb) + (long long)r * n,
                                reinterpret_cast<double2*>(Vb) + (long long)r * (m + 1) * n, 0, n, 1, scal_d + r, st)))
             return rc;
     }
@@ -242,7 +243,7 @@ int Solver::start_deflated(int r) {
     // last column of G_{k+1}: the explicit residual in the old basis, V_{m+1}^H r
     {
         ProfScope ps(&ctx->prof, "multidot", (double)(mm + 2) * fb);
-        if ((rc = launch_multidot(vref_all(r, 0), field_vec(rb, r), n, nullptr, mm + 1, m + 1, 1, partial, nblk,
+        if ((rc = launch_multidot(op, vref_all(r, 0), field_vec(rb, r), n, nullptr, mm + 1, m + 1, 1, partial, nblk,
                                   dots, st)))
             return rc;
     }
@@ -278,7 +279,7 @@ int Solver::start_deflated(int r) {
     DW_CUDA_TRY(cudaMemcpyAsync(Qd, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice, st));
     {
         ProfScope ps(&ctx->prof, "rotate_V", (double)(mm + 1 + k1) * fb);
-        if ((rc = launch_rotate(P64, Vb + (long long)r * (m + 1) * fb, 0, fb, V, 1, nullptr, mm + 1, k1, Qd, m + 1,
+        if ((rc = launch_rotate(op, Vb + (long long)r * (m + 1) * fb, 0, fb, V, 1, nullptr, mm + 1, k1, Qd, m + 1,
                                 nullptr, st)))
             return rc;
     }
@@ -294,19 +295,21 @@ int Solver::start_deflated(int r) {
     for (int pass = 0; pass < 2; ++pass) {
         ProfScope ps(&ctx->prof, "cgs", (double)(2 * k + 3) * fb);
         VecRef w = vref_all(r, k);
-        if ((rc = launch_multidot(vref_all(r, 0), w, n, nullptr, k, m + 1, 1, partial, nblk, dots, st))) return rc;
-        if ((rc = launch_multiaxpy(vref_all(r, 0), w, n, nullptr, k, 1, dots, NP, partial, nblk, norm2d + r, st)))
+        if ((rc = launch_multidot(op, vref_all(r, 0), w, n, nullptr, k, m + 1, 1, partial, nblk, dots, st)))
+            return rc;
+        if ((rc = launch_multiaxpy(op, vref_all(r, 0), w, n, nullptr, k, 1, dots, NP, partial, nblk, norm2d + r,
+                                   st)))
             return rc;
     }
     {
         ProfScope ps(&ctx->prof, "normalize", 2.0 * fb);
         VecRef w = vref_all(r, k);
-        if ((rc = launch_normalize(w, w, n, nullptr, 1, norm2d + r, st))) return rc;
+        if ((rc = launch_normalize(op, w, w, V, nullptr, 1, norm2d + r, -1, FieldRef{}, st))) return rc;
     }
     // c = [V_{k+1}^H r; 0]
     {
         ProfScope ps(&ctx->prof, "multidot", (double)(k1 + 1) * fb);
-        if ((rc = launch_multidot(vref_all(r, 0), field_vec(rb, r), n, nullptr, k1, m + 1, 1, partial, nblk, dots,
+        if ((rc = launch_multidot(op, vref_all(r, 0), field_vec(rb, r), n, nullptr, k1, m + 1, 1, partial, nblk, dots,
                                   st)))
             return rc;
     }
@@ -342,21 +345,21 @@ int Solver::cycle_end(int r) {
     DW_CUDA_TRY(cudaMemcpyAsync(nz_d, &mm, sizeof(int), cudaMemcpyHostToDevice, st));
     {
         ProfScope ps(&ctx->prof, "xupdate", (double)mm * sb + 2.0 * fb);
-        if ((rc = launch_xupdate(sp, Zb + (long long)r * m * sb, 0, sb, reinterpret_cast<double2*>(xb) + (long long)r * n,
-                                 0, V, 1, nz_d, etad, 0, st)))
+        if ((rc = launch_xupdate(sp, op, Zb + (long long)r * m * sb, 0, sb,
+                                 reinterpret_cast<double2*>(xb) + (long long)r * n, 0, V, 1, nz_d, etad, 0, st)))
             return rc;
     }
     // explicit FP64 residual r = b - D x
     {
-        ProfScope ps(&ctx->prof, "dw_f64_residual", ptr_bytes_dw(P64, P64, P64, V) + fb);
+        ProfScope ps(&ctx->prof, "dw_f64_residual", ptr_bytes_dw(op, op, P64, V) + fb);
         FieldRef in{xb + (long long)r * fb, 0, 0, 0}, out{rb + (long long)r * fb, 0, 0, 0},
             sub{bb + (long long)r * fb, 0, 0, 0};
-        if ((rc = launch_dw(P64, P64, P64, g, ctx->m0, in, out, U64, nullptr, 1, &sub, st))) return rc;
+        if ((rc = launch_dw(op, op, P64, g, ctx->m0, in, out, U64, nullptr, 1, &sub, st))) return rc;
     }
     explicit_res++;
     {
         ProfScope ps(&ctx->prof, "norm2", (double)fb);
-        if ((rc = launch_norm2(reinterpret_cast<double2*>(rb) + (long long)r * n, 0, n, 1, partial, nblk,
+        if ((rc = launch_norm2(op, reinterpret_cast<double2*>(rb) + (long long)r * n, 0, n, 1, partial, nblk,
                                norm2d + r, st)))
             return rc;
     }
@@ -400,7 +403,7 @@ int Solver::step() {
     // z_j = M v_j
     {
         ProfScope ps(&ctx->prof, "convert_v", (double)nact * (fb + sb));
-        if ((rc = launch_convert(P64, sp, Vf, Lf, V, jtab_d, nrhs, st))) return rc;
+        if ((rc = launch_convert(op, sp, Vf, Lf, V, jtab_d, nrhs, st))) return rc;
     }
     for (int cyc = 0; cyc < P.sap_cycles; ++cyc)
         for (int colour = 0; colour < 2; ++colour) {
@@ -415,8 +418,8 @@ int Solver::step() {
     // w = D z_j  (written into column j+1 of V)
     {
         const int pl = (mp == P64) ? P64 : P32;
-        ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(sp, P64, pl, V));
-        if ((rc = launch_dw(sp, P64, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st))) return rc;
+        ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(sp, op, pl, V));
+        if ((rc = launch_dw(sp, op, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st))) return rc;
     }
     // classical Gram-Schmidt, pass 1
     double jsum = 0;
@@ -424,10 +427,11 @@ int Solver::step() {
         if (jtab_h[r] >= 0) jsum += jtab_h[r] + 1;
     {
         ProfScope ps(&ctx->prof, "cgs", (2.0 * jsum + 3.0 * nact) * fb);
-        if ((rc = launch_multidot(vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots, st)))
+        if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
+                                  st)))
             return rc;
-        if ((rc = launch_multiaxpy(vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk, norm2d,
-                                   st)))
+        if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
+                                   norm2d, st)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
@@ -456,10 +460,11 @@ int Solver::step() {
         for (int r = 0; r < nrhs; ++r)
             if (j2[r] >= 0) js2 += j2[r] + 1, ++n2;
         ProfScope ps(&ctx->prof, "cgs", (2.0 * js2 + 3.0 * n2) * fb);
-        if ((rc = launch_multidot(vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots, st)))
+        if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
+                                  st)))
             return rc;
-        if ((rc = launch_multiaxpy(vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk, norm2d,
-                                   st)))
+        if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
+                                   norm2d, st)))
             return rc;
         DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
         DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -473,7 +478,8 @@ int Solver::step() {
     DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
     {
         ProfScope ps(&ctx->prof, "normalize", (double)nact * 2.0 * fb);
-        if ((rc = launch_normalize(vref_all(0, 1), vref_all(0, 1), n, jtab_d, nrhs, norm2d, st))) return rc;
+        if ((rc = launch_normalize(op, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, -1, FieldRef{}, st)))
+            return rc;
     }
     // host: Hessenberg column, Givens update, end-of-cycle tests
     for (int r = 0; r < nrhs; ++r) {
@@ -527,26 +533,26 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
         DW_CUDA_TRY(cudaMemcpyAsync(W->canon.p, b_user, canon_bytes, cudaMemcpyHostToDevice, st));
         b_dev = W->canon.as<double>();
     }
-    if ((rc = launch_to_internal(P64, b_dev, bb, V, nrhs, st))) return rc;
+    if ((rc = launch_to_internal(op, b_dev, bb, V, nrhs, st))) return rc;
     if (P.use_x0) {
         if (P.host_buffers) {
             if ((rc = sync())) return rc;
             DW_CUDA_TRY(cudaMemcpyAsync(W->canon.p, x_user, canon_bytes, cudaMemcpyHostToDevice, st));
             x_dev = W->canon.as<double>();
         }
-        if ((rc = launch_to_internal(P64, x_dev, xb, V, nrhs, st))) return rc;
+        if ((rc = launch_to_internal(op, x_dev, xb, V, nrhs, st))) return rc;
         FieldRef in{xb, fb, 0, 0}, out{rb, fb, 0, 0}, sub{bb, fb, 0, 0};
-        if ((rc = launch_dw(P64, P64, P64, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st))) return rc;
+        if ((rc = launch_dw(op, op, P64, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st))) return rc;
         explicit_res++;
     } else {
         DW_CUDA_TRY(cudaMemsetAsync(xb, 0, (size_t)nrhs * fb, st));
         DW_CUDA_TRY(cudaMemcpyAsync(rb, bb, (size_t)nrhs * fb, cudaMemcpyDeviceToDevice, st));
     }
-    if ((rc = launch_norm2(reinterpret_cast<double2*>(bb), n, n, nrhs, partial, nblk, norm2d, st))) return rc;
+    if ((rc = launch_norm2(op, reinterpret_cast<double2*>(bb), n, n, nrhs, partial, nblk, norm2d, st))) return rc;
     DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     if ((rc = sync())) return rc;
     std::vector<double> bn(norm2_h, norm2_h + nrhs);
-    if ((rc = launch_norm2(reinterpret_cast<double2*>(rb), n, n, nrhs, partial, nblk, norm2d, st))) return rc;
+    if ((rc = launch_norm2(op, reinterpret_cast<double2*>(rb), n, n, nrhs, partial, nblk, norm2d, st))) return rc;
     DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     if ((rc = sync())) return rc;
     for (int r = 0; r < nrhs; ++r) {
@@ -571,10 +577,10 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
     }
     // result back to the caller's layout
     if (P.host_buffers) {
-        if ((rc = launch_from_internal(P64, xb, W->canon.as<double>(), V, nrhs, st))) return rc;
+        if ((rc = launch_from_internal(op, xb, W->canon.as<double>(), V, nrhs, st))) return rc;
         DW_CUDA_TRY(cudaMemcpyAsync(x_user, W->canon.p, canon_bytes, cudaMemcpyDeviceToHost, st));
     } else {
-        if ((rc = launch_from_internal(P64, xb, x_user, V, nrhs, st))) return rc;
+        if ((rc = launch_from_internal(op, xb, x_user, V, nrhs, st))) return rc;
     }
     if ((rc = sync())) return rc;
     int status = DW_OK, conv = 0;

@@ -32,7 +32,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*([a-z_][a-z_0-9]*)\s*\(", txt, re.M):
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][A-Za-z_0-9]*[\s*]+)+([a-z_][a-z_0-9]*)\s*\(", txt, re.M):
             names.add(m.group(1))
     return sorted(names)
 

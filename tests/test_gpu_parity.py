@@ -151,13 +151,15 @@ def _solve(dw, cfg, U, b, nrhs=1, **kw):
         c.close()
 
 
-def test_fgmresdr_fp64_matches_oracle_iterates(dw):
+@pytest.mark.parametrize("outer", [0, 4])
+def test_fgmresdr_fp64_matches_oracle_iterates(dw, outer):
     """FP64 SAP and FP64 Arnoldi product: same decisions as the oracle, so the
-    same number of iterations and cycles, and the same solution to ~cond*eps."""
+    same number of iterations and cycles, and the same solution to ~cond*eps
+    (outer vectors in FP64, or double-float with a 48-bit significand)."""
     cfg, U, b = _tiny()
     ref = oracle.solve(U, b, cfg["dims"], cfg["block"], cfg["m0"], cfg["sap_cycles"], cfg["mr_steps"], cfg["m"],
                        cfg["k"], cfg["tol"])
-    x, S = _solve(dw, cfg, U, b, sap_prec=0, matvec_prec=0)
+    x, S = _solve(dw, cfg, U, b, sap_prec=0, matvec_prec=0, outer_prec=outer)
     assert S.converged == 1
     assert S.iterations == ref.iterations and S.cycles == ref.cycles
     assert rel2(x.reshape(-1), ref.x) <= 1e-9
@@ -184,13 +186,14 @@ def test_fgmresdr_low_precision_sap_converges(dw, sap_prec):
 
 
 @pytest.mark.parametrize("k", [0, 3])
-def test_fgmresdr_batched_equals_single(dw, k):
+@pytest.mark.parametrize("outer", [0, 4])
+def test_fgmresdr_batched_equals_single(dw, k, outer):
     cfg, U, _ = _tiny()
     bs = fg.gaussian_source(cfg["dims"], 7, nrhs=3)
-    xb, Sb = _solve(dw, cfg, U, bs, nrhs=3, k=k)
+    xb, Sb = _solve(dw, cfg, U, bs, nrhs=3, k=k, outer_prec=outer)
     assert Sb.converged == 3
     for r in range(3):
-        x1, S1 = _solve(dw, cfg, U, bs[r], k=k)
+        x1, S1 = _solve(dw, cfg, U, bs[r], k=k, outer_prec=outer)
         assert S1.iterations == Sb.iterations_rhs[r]
         assert rel2(xb[r].reshape(-1), x1.reshape(-1)) <= 1e-12
 
