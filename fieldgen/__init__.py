@@ -123,12 +123,44 @@ def random_su3(V: int, seed: int) -> np.ndarray:
     return Q
 
 
-def lattice_configs():
-    """The five synthetic workloads (lattice, field strength, solver settings).
+def spectral_edges() -> dict:
+    """Left spectral edges of D at m0 = 0 for the stored synthetic fields
+    (written by ``python -m oracle.tune_masses``; Ritz values of the oracle)."""
+    import json
+    import os
 
-    ``m0`` is ``None`` where it is tuned from the spectrum (see ``oracle.tune``)
-    and stored alongside the tests.
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "spectral_edges.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
+def edge_key(dims, eps, seed) -> str:
+    return f"{'x'.join(map(str, dims))}_eps{eps}_seed{seed}"
+
+
+def tuned_m0(dims, eps, seed, target):
+    """Bare mass putting the left spectral edge of D at ``target``
+    (spec(D_m0) = spec(D_0) + m0), or None if the edge is not stored."""
+    e = spectral_edges().get(edge_key(dims, eps, seed))
+    return None if e is None else target - e["edge_re"]
+
+
+def lattice_configs():
+    """The synthetic workloads (lattice, field strength, solver settings).
+
+    ``m0`` of the larger lattices puts the left spectral edge of D (found by
+    Arnoldi on the oracle's operator) at ``target_min_abs_eig``.
     """
+    cfg = _configs()
+    for c in cfg.values():
+        if c.get("m0") is None:
+            c["m0"] = tuned_m0(c["dims"], c["eps"], c["seed"], c["target_min_abs_eig"])
+    return cfg
+
+
+def _configs():
     return {
         "tiny_4x4x4x4": dict(dims=(4, 4, 4, 4), eps=0.3, seed=0, m0=-0.5, block=(2, 2, 2, 2),
                               sap_cycles=4, mr_steps=4, m=20, k=5, tol=1e-10, nrhs=1),

@@ -386,6 +386,43 @@ def solve(U, b, dims, block, m0, sap_cycles, mr_steps, m, k, tol, **kw) -> Solve
     return fgmresdr(A, M, np.asarray(b).reshape(-1), m, k, tol, **kw)
 
 
+def arnoldi_ritz(apply, n: int, m: int, seed: int = 0):
+    """Ritz values of an m-step Arnoldi process (classical Gram-Schmidt with one
+    reorthogonalisation) started from a seeded random vector, with their
+    residual bounds |h_{m+1,m} e_m^T y|. Exterior eigenvalues converge first."""
+    rng = np.random.default_rng(seed)
+    V = np.zeros((m + 1, n), dtype=np.complex128)
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    V[0] = v / np.linalg.norm(v)
+    for j in range(m):
+        w = np.asarray(apply(V[j]), dtype=np.complex128)
+        for _ in range(2):
+            h = (V[:j + 1] @ w.conj()).conj()  # V^H w without copying V
+            w = w - V[:j + 1].T @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        V[j + 1] = w / H[j + 1, j]
+    theta, Y = np.linalg.eig(H[:m, :m])
+    bounds = np.abs(H[m, m - 1] * Y[m - 1, :])
+    return theta, bounds
+
+
+def tune_m0_arnoldi(U, dims, target: float, m: int = 200, seed: int = 0):
+    """Bare mass from the leftmost Ritz value of D at m0 = 0.
+
+    spec(D_m0) = spec(D_0) + m0, so m0 = target - Re(theta*) with theta* the
+    Ritz value of smallest real part of an m-step Arnoldi process on D_0.
+    Returns (m0, theta*, its residual bound, seconds)."""
+    V = int(np.prod(dims))
+    U = _cvec(U)
+    t0 = time.time()
+    theta, bounds = arnoldi_ritz(
+        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0).reshape(-1), 12 * V, m, seed)
+    i = int(np.argmin(theta.real))
+    return target - theta[i].real, theta[i], bounds[i], time.time() - t0
+
+
 def tune_m0(U, dims, target: float, nev: int = 6, ncv: int = 48, tol: float = 1e-6):
     """Bare mass with smallest |eigenvalue| of D_m0 near ``target``.
 

@@ -74,6 +74,7 @@ struct Elem<P64> {
     static __device__ __forceinline__ C warp_reduce(C a) { return C{warp_sum(a.re), warp_sum(a.im)}; }
     static __device__ __forceinline__ C scale(C a, double s) { return C{a.re * s, a.im * s}; }
     static __device__ __forceinline__ cx<float> to_f(C a) { return mk<float>((float)a.re, (float)a.im); }
+    static __device__ __forceinline__ C add(C a, C b) { return C{a.re + b.re, a.im + b.im}; }
 };
 
 template <>
@@ -120,60 +121,106 @@ struct Elem<PDF> {
     static __device__ __forceinline__ C warp_reduce(C a) { return C{df_warp_sum(df_norm(a.re)), df_warp_sum(df_norm(a.im))}; }
     static __device__ __forceinline__ C scale(C a, df s) { return C{df_mul(a.re, s), df_mul(a.im, s)}; }
     static __device__ __forceinline__ cx<float> to_f(C a) { return mk<float>(a.re.hi + a.re.lo, a.im.hi + a.im.lo); }
+    static __device__ __forceinline__ C add(C a, C b) { return C{df_add(a.re, b.re), df_add(a.im, b.im)}; }
 };
 
 // ---- multi-dot: partial[r][blk][i] = <V_i, w> (i < nv), [nvmax] = ||w||^2 ---
+// Each CTA stages a chunk of w in shared memory; warp q owns basis vectors
+// i = q, q + 8, q + 16, ... and sweeps them over the chunk with its lanes, so
+// every V_i element is read once, coalesced, and the warp reductions happen
+// once per CTA at the end.
+constexpr int kChunk = 2048;
+constexpr int kMD = 1024;  // threads per multi-dot CTA: 32 warps, at most 2 vectors per warp
+
 template <int VP>
-__global__ void __launch_bounds__(kT) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off,
-                                                      int nvmax, double2* partial) {
+__global__ void __launch_bounds__(kMD, 1) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
+                                                          int nv_off, int nvmax, double2* partial) {
     typedef Elem<VP> E;
     typedef typename E::C C;
-    __shared__ double2 sh[kMaxV + 1][kT / 32];
+    typedef typename E::T T16;
+    __shared__ T16 ws[kChunk];
+    __shared__ double red[kMD / 32];
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
     const int nv = rhs_nv(jtab, r, nv_off);
     const int j = jtab ? jtab[r] : 0;
-    const double2* Vr = Vb.base + r * Vb.rhs_stride;
-    const double2* wr = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * kT;
-    const long long e0 = (long long)blockIdx.x * kT + threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NW = kMD / 32;
+    const double2* Vr = Vb.base + r * Vb.rhs_stride + (long long)Vb.col_off * Vb.col_stride;
+    const T16* wr = reinterpret_cast<const T16*>(w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride);
+    const int R = (nv > warp) ? (nv - warp + NW - 1) / NW : 0;  // vectors of this warp (<= 2)
+    const double2* v0 = Vr + (long long)warp * Vb.col_stride;
+    const double2* v1 = Vr + (long long)(warp + NW) * Vb.col_stride;
+    C a0 = E::zero(), a1 = E::zero();
     typename E::N wacc = E::nzero();
-    for (int g0 = 0; g0 < nv || g0 == 0; g0 += kGroup) {
-        C acc[kGroup];
-#pragma unroll
-        for (int q = 0; q < kGroup; ++q) acc[q] = E::zero();
-        const int gn = min(kGroup, nv - g0);
-        for (long long e = e0; e < n; e += stride) {
-            const C wv = E::load(wr, e);
-            if (g0 == 0) E::norm2_acc(wacc, wv);
-#pragma unroll
-            for (int q = 0; q < kGroup; ++q)
-                if (q < gn) {
-                    const double2* vi = Vr + (long long)(g0 + q + Vb.col_off) * Vb.col_stride;
-                    E::mac_conj(acc[q], E::load(vi, e), wv);
-                }
-        }
-#pragma unroll
-        for (int q = 0; q < kGroup; ++q)
-            if (q < gn) {
-                const C t = E::warp_reduce(acc[q]);
-                if (lane == 0) sh[g0 + q][warp] = E::to_d2(t);
+    for (long long c0 = (long long)blockIdx.x * kChunk; c0 < n; c0 += (long long)gridDim.x * kChunk) {
+        const int cn = (int)min((long long)kChunk, n - c0);
+        __syncthreads();  // the previous chunk is no longer read
+        for (int k = t; k < kChunk; k += kMD) {
+            T16 v;
+            if (k < cn) {
+                v = wr[c0 + k];
+                E::norm2_acc(wacc, E::load_rw(reinterpret_cast<const double2*>(&v), 0));
+            } else {
+                v = T16{};
             }
-        if (nv == 0) break;
+            ws[k] = v;
+        }
+        __syncthreads();
+        if (R == 0) continue;
+        int k = lane;
+        for (; k + 96 < cn; k += 128) {  // four elements per lane in flight
+            C x0 = E::load(v0, c0 + k), x1 = E::load(v0, c0 + k + 32), x2 = E::load(v0, c0 + k + 64),
+              x3 = E::load(v0, c0 + k + 96);
+            C y0, y1, y2, y3;
+            if (R > 1) {
+                y0 = E::load(v1, c0 + k);
+                y1 = E::load(v1, c0 + k + 32);
+                y2 = E::load(v1, c0 + k + 64);
+                y3 = E::load(v1, c0 + k + 96);
+            }
+            T16 r0 = ws[k], r1 = ws[k + 32], r2 = ws[k + 64], r3 = ws[k + 96];
+            const C w0 = E::load_rw(reinterpret_cast<const double2*>(&r0), 0);
+            const C w1 = E::load_rw(reinterpret_cast<const double2*>(&r1), 0);
+            const C w2 = E::load_rw(reinterpret_cast<const double2*>(&r2), 0);
+            const C w3 = E::load_rw(reinterpret_cast<const double2*>(&r3), 0);
+            E::mac_conj(a0, x0, w0);
+            E::mac_conj(a0, x1, w1);
+            E::mac_conj(a0, x2, w2);
+            E::mac_conj(a0, x3, w3);
+            if (R > 1) {
+                E::mac_conj(a1, y0, w0);
+                E::mac_conj(a1, y1, w1);
+                E::mac_conj(a1, y2, w2);
+                E::mac_conj(a1, y3, w3);
+            }
+        }
+        for (; k < cn; k += 32) {
+            T16 rr = ws[k];
+            const C wv = E::load_rw(reinterpret_cast<const double2*>(&rr), 0);
+            E::mac_conj(a0, E::load(v0, c0 + k), wv);
+            if (R > 1) E::mac_conj(a1, E::load(v1, c0 + k), wv);
+        }
     }
-    const double wn = warp_sum(E::nfin(wacc));
-    if (lane == 0) sh[kMaxV][warp] = make_double2(wn, 0.0);
-    __syncthreads();
     const int NP = nvmax + 1;
     double2* out = partial + ((long long)r * gridDim.x + blockIdx.x) * NP;
-    for (int i = threadIdx.x; i < NP; i += kT) {
-        const int src = (i == nvmax) ? kMaxV : i;
-        double2 s = make_double2(0.0, 0.0);
-        if (i < nv || i == nvmax)
-            for (int q = 0; q < kT / 32; ++q) s.x += sh[src][q].x, s.y += sh[src][q].y;
-        out[i] = s;
+    if (R > 0) {
+        const C s0 = E::warp_reduce(a0);
+        if (lane == 0) out[warp] = E::to_d2(s0);
     }
+    if (R > 1) {
+        const C s1 = E::warp_reduce(a1);
+        if (lane == 0) out[warp + NW] = E::to_d2(s1);
+    }
+    const double wn = warp_sum(E::nfin(wacc));
+    if (lane == 0) red[warp] = wn;
+    __syncthreads();
+    if (t == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < NW; ++q) sum += red[q];
+        out[nvmax] = make_double2(sum, 0.0);
+    }
+    for (int i = nv + t; i < nvmax; i += kMD) out[i] = make_double2(0.0, 0.0);
 }
 
 // out[r][i] = sum_blk partial[r][blk][i] in fixed order
@@ -247,6 +294,7 @@ __global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, lon
                                                        const double* norm2, FieldRef low) {
     typedef Elem<VP> E;
     typedef typename E::C C;
+    typedef typename real_of<(PS == P64) ? P64 : P32>::type CL;  // precision of the SAP copy
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
     const long long s = (long long)blockIdx.x * kT + threadIdx.x;
@@ -256,24 +304,22 @@ __global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, lon
     const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
     const double2* src = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
     double2* out = dst.base + r * dst.rhs_stride + (long long)(j + dst.col_off) * dst.col_stride;
-    cx<float> f[12];
-    if constexpr (VP == PDF) {
-        const df sc = df_from_double(inv);
+    cx<CL> f[12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            C v = E::scale(E::load_rw(src, c * V + s), sc);
-            E::store(out, c * V + s, v);
+    for (int c = 0; c < 12; ++c) {
+        C v;
+        if constexpr (VP == PDF)
+            v = E::scale(E::load_rw(src, c * V + s), df_from_double(inv));
+        else
+            v = E::scale(E::load_rw(src, c * V + s), inv);
+        E::store(out, c * V + s, v);
+        const double2 d = E::to_d2(v);
+        if constexpr (sizeof(CL) == 8)
+            f[c] = mk<CL>(d.x, d.y);
+        else
             f[c] = E::to_f(v);
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            C v = E::scale(E::load_rw(src, c * V + s), inv);
-            E::store(out, c * V + s, v);
-            f[c] = E::to_f(v);
-        }
     }
-    if constexpr (PS >= 0) store_spinor<PS, float>(field_ptr(low, jtab, r), V, s, f);
+    if constexpr (PS >= 0) store_spinor<PS, CL>(field_ptr(low, jtab, r), V, s, f);
 }
 
 template <int VP>
@@ -464,13 +510,18 @@ int blas_nblk(long long n) { return (int)grid_for(n); }
 int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
                     double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
+    if (nvmax > 2 * (kMD / 32)) return fail(DW_EINVAL, "multi-dot handles at most 64 vectors");
     if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    // one chunk of w per CTA and sweep, at most three CTAs per SM, never more than partial[] holds
+    long long nb = (n + kChunk - 1) / kChunk;
+    if (nb > 152LL) nb = 152LL;
+    if (nb > nblk) nb = nblk;
     if (vp == PDF)
-        multidot_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
+        multidot_kernel<PDF><<<dim3((unsigned)nb, nrhs), kMD, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
     else
-        multidot_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
+        multidot_kernel<P64><<<dim3((unsigned)nb, nrhs), kMD, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
     DW_LAUNCH_CHECK();
-    finalize_kernel<<<nrhs, kT, 0, st>>>(partial, nblk, nvmax + 1, jtab, out);
+    finalize_kernel<<<nrhs, kT, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
     DW_LAUNCH_CHECK();
     return DW_OK;
 }
@@ -505,6 +556,7 @@ int launch_normalize(int vp, VecRef w, VecRef dst, long long V, const int* jtab,
     NORM(P64, P16)
     NORM(P64, PB16)
     NORM(PDF, -1)
+    NORM(PDF, P64)
     NORM(PDF, P32)
     NORM(PDF, P16)
     NORM(PDF, PB16)

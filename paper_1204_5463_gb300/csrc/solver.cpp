@@ -149,7 +149,7 @@ int Solver::setup() {
     if ((rc = W->vlow.ensure((size_t)nrhs * sb))) return rc;
     if ((rc = W->zscr.ensure((size_t)(k > 0 ? k : 1) * sb))) return rc;
     if ((rc = W->partial.ensure((size_t)nrhs * nblk * NP * sizeof(double2)))) return rc;
-    if ((rc = W->dots.ensure((size_t)nrhs * NP * sizeof(double2)))) return rc;
+    if ((rc = W->dots.ensure((size_t)2 * nrhs * NP * sizeof(double2)))) return rc;
     if ((rc = W->Q.ensure((size_t)(m + 1) * (m + 1) * sizeof(double2)))) return rc;
     if ((rc = W->eta.ensure((size_t)(m + 1) * sizeof(double2)))) return rc;
     if ((rc = W->norm2.ensure((size_t)nrhs * sizeof(double)))) return rc;
@@ -163,7 +163,7 @@ int Solver::setup() {
         W->dots_h = nullptr;
         W->norm2_h = nullptr;
         W->jtab_h = nullptr;
-        DW_CUDA_TRY(cudaMallocHost(&W->dots_h, (size_t)DW_MAX_RHS * 66 * sizeof(double2)));
+        DW_CUDA_TRY(cudaMallocHost(&W->dots_h, (size_t)2 * DW_MAX_RHS * 66 * sizeof(double2)));
         DW_CUDA_TRY(cudaMallocHost(&W->norm2_h, (size_t)DW_MAX_RHS * sizeof(double)));
         DW_CUDA_TRY(cudaMallocHost(&W->jtab_h, (size_t)DW_MAX_RHS * sizeof(int)));
         W->dots_h_n = (size_t)DW_MAX_RHS * 66;
@@ -201,13 +201,13 @@ static double ptr_bytes_dw(int pin, int pout, int plink, long long V) {
 // plain first cycle (or clean restart) from the explicit residual in rb[r]
 int Solver::start_plain(int r) {
     RhsState& s = R[r];
-    const double inv = 1.0 / s.rnorm;
-    DW_CUDA_TRY(cudaMemcpyAsync(scal_d + r, &inv, sizeof(double), cudaMemcpyHostToDevice, st));
+    const double nn = s.rnorm * s.rnorm;
+    DW_CUDA_TRY(cudaMemcpyAsync(scal_d + r, &nn, sizeof(double), cudaMemcpyHostToDevice, st));
     int rc;
     {
-        ProfScope ps(&ctx->prof, "scale", 2.0 * fb);
-        if ((rc = launch_scale(op, reinterpret_cast<double2*>(rb) + (long long)r * n,
-                               reinterpret_cast<double2*>(Vb) + (long long)r * (m + 1) * n, 0, n, 1, scal_d + r, st)))
+        ProfScope ps(&ctx->prof, "normalize", 2.0 * fb + sb);
+        const FieldRef low{vlow + (long long)r * sb, 0, 0, 0};
+        if ((rc = launch_normalize(op, field_vec(rb, r), vref_all(r, 0), V, nullptr, 1, scal_d + r, sp, low, st)))
             return rc;
     }
     std::fill(s.H.begin(), s.H.end(), zd(0));
@@ -304,7 +304,8 @@ int Solver::start_deflated(int r) {
     {
         ProfScope ps(&ctx->prof, "normalize", 2.0 * fb);
         VecRef w = vref_all(r, k);
-        if ((rc = launch_normalize(op, w, w, V, nullptr, 1, norm2d + r, -1, FieldRef{}, st))) return rc;
+        const FieldRef low{vlow + (long long)r * sb, 0, 0, 0};
+        if ((rc = launch_normalize(op, w, w, V, nullptr, 1, norm2d + r, sp, low, st))) return rc;
     }
     // c = [V_{k+1}^H r; 0]
     {
@@ -396,15 +397,10 @@ int Solver::step() {
     }
     if (nact == 0) return fail(DW_EBREAKDOWN, "no right-hand side left to step");
     DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-    const FieldRef Vf{Vb, (m + 1) * fb, fb, 0};
     const FieldRef Vf1{Vb, (m + 1) * fb, fb, 1};
     const FieldRef Zf{Zb, m * sb, sb, 0};
     const FieldRef Lf{vlow, sb, 0, 0};
-    // z_j = M v_j
-    {
-        ProfScope ps(&ctx->prof, "convert_v", (double)nact * (fb + sb));
-        if ((rc = launch_convert(op, sp, Vf, Lf, V, jtab_d, nrhs, st))) return rc;
-    }
+    // z_j = M v_j  (v_j was written in SAP storage to vlow when it was normalised)
     for (int cyc = 0; cyc < P.sap_cycles; ++cyc)
         for (int colour = 0; colour < 2; ++colour) {
             const int mode = (cyc > 0) ? 2 : (colour == 0 ? 0 : 1);
@@ -421,15 +417,20 @@ int Solver::step() {
         ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(sp, op, pl, V));
         if ((rc = launch_dw(sp, op, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st))) return rc;
     }
-    // classical Gram-Schmidt, pass 1
+    // classical Gram-Schmidt: h = V^H w, w' = w - V h; a second projection
+    // ("twice is enough") only where cancellation could cost orthogonality at
+    // the working precision: u / (||w'|| / ||w||) > 1e-13
     double jsum = 0;
     for (int r = 0; r < nrhs; ++r)
         if (jtab_h[r] >= 0) jsum += jtab_h[r] + 1;
     {
-        ProfScope ps(&ctx->prof, "cgs", (2.0 * jsum + 3.0 * nact) * fb);
+        ProfScope ps(&ctx->prof, "cgs_project", (jsum + nact) * fb);
         if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
                                   st)))
             return rc;
+    }
+    {
+        ProfScope ps(&ctx->prof, "cgs_update", (jsum + 2.0 * nact) * fb);
         if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
                                    norm2d, st)))
             return rc;
@@ -437,6 +438,7 @@ int Solver::step() {
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
     DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     if ((rc = sync())) return rc;
+    const double unit = (op == PDF) ? 3.552713678800501e-15 : 1.1102230246251565e-16;
     std::vector<std::vector<zd>> h(nrhs);
     bool need2 = false;
     for (int r = 0; r < nrhs; ++r) {
@@ -445,40 +447,45 @@ int Solver::step() {
         h[r].resize(j + 2);
         for (int i = 0; i <= j; ++i) h[r][i] = zd(dots_h[lin(r, i)].x, dots_h[lin(r, i)].y);
         R[r].wn0 = std::sqrt(dots_h[lin(r, m + 1)].x);
-        const double wn1 = std::sqrt(norm2_h[r]);
-        const bool re = wn1 < 0.7 * R[r].wn0;  // cancellation: orthogonalise once more
+        const double ratio = std::sqrt(norm2_h[r]) / (R[r].wn0 > 0 ? R[r].wn0 : 1.0);
+        const bool re = unit > 1e-13 * ratio;
         need2 |= re;
-        if (!re) jtab_h[r] = -1 - j;          // encode "stepping, no second pass"
+        if (!re) jtab_h[r] = -1;
     }
     if (need2) {
-        std::vector<int> j2(nrhs);
-        for (int r = 0; r < nrhs; ++r) j2[r] = jtab_h[r] >= 0 ? jtab_h[r] : -1;
-        std::memcpy(jtab_h, j2.data(), sizeof(int) * nrhs);
         DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
         double js2 = 0;
         int n2 = 0;
         for (int r = 0; r < nrhs; ++r)
-            if (j2[r] >= 0) js2 += j2[r] + 1, ++n2;
-        ProfScope ps(&ctx->prof, "cgs", (2.0 * js2 + 3.0 * n2) * fb);
-        if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
-                                  st)))
-            return rc;
-        if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
-                                   norm2d, st)))
-            return rc;
+            if (jtab_h[r] >= 0) js2 += jtab_h[r] + 1, ++n2;
+        std::vector<double> keep(norm2_h, norm2_h + nrhs);
+        {
+            ProfScope ps(&ctx->prof, "cgs_reorth", (2.0 * js2 + 3.0 * n2) * fb);
+            if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk,
+                                      dots, st)))
+                return rc;
+            if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial,
+                                       nblk, norm2d, st)))
+                return rc;
+        }
         DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
         DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
         if ((rc = sync())) return rc;
-        for (int r = 0; r < nrhs; ++r)
-            if (j2[r] >= 0)
-                for (int i = 0; i <= j2[r]; ++i) h[r][i] += zd(dots_h[lin(r, i)].x, dots_h[lin(r, i)].y);
+        for (int r = 0; r < nrhs; ++r) {
+            if (jtab_h[r] < 0) {
+                norm2_h[r] = keep[r];
+                continue;
+            }
+            for (int i = 0; i <= jtab_h[r]; ++i) h[r][i] += zd(dots_h[lin(r, i)].x, dots_h[lin(r, i)].y);
+        }
     }
-    // restore the step's column table and normalise v_{j+1} = w / ||w||
+    // restore the step's column table; v_{j+1} = w / ||w|| (also into SAP storage)
     for (int r = 0; r < nrhs; ++r) jtab_h[r] = (!R[r].done && R[r].j >= 0) ? R[r].j : -1;
     DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    DW_CUDA_TRY(cudaMemcpyAsync(norm2d, norm2_h, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
-        ProfScope ps(&ctx->prof, "normalize", (double)nact * 2.0 * fb);
-        if ((rc = launch_normalize(op, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, -1, FieldRef{}, st)))
+        ProfScope ps(&ctx->prof, "normalize", (double)nact * (2.0 * fb + sb));
+        if ((rc = launch_normalize(op, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, sp, Lf, st)))
             return rc;
     }
     // host: Hessenberg column, Givens update, end-of-cycle tests
