@@ -44,6 +44,17 @@ void DevBuf::release() {
 }
 
 // ---------------------------------------------------------------------------
+cudaEvent_t Profiler::take() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
 int Profiler::begin(const char* name, double bytes, cudaEvent_t* start_out, int* idx) {
     int i = 0;
     for (; i < (int)k.size(); ++i)
@@ -52,8 +63,8 @@ int Profiler::begin(const char* name, double bytes, cudaEvent_t* start_out, int*
         k.emplace_back();
         k.back().name = name;
     }
-    cudaEvent_t a;
-    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    cudaEvent_t a = take();
+    if (!a) return -1;
     cudaEventRecord(a, stream);
     *start_out = a;
     *idx = i;
@@ -62,8 +73,11 @@ int Profiler::begin(const char* name, double bytes, cudaEvent_t* start_out, int*
 }
 
 void Profiler::end(int idx, cudaEvent_t start) {
-    cudaEvent_t b;
-    if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEvent_t b = take();
+    if (!b) {
+        pool.push_back(start);
+        return;
+    }
     cudaEventRecord(b, stream);
     k[idx].pending.push_back({start, b});
 }
@@ -77,8 +91,8 @@ void Profiler::drain() {
             e.total_ms += ms;
             e.launches += 1;
             e.bytes += (i < e.pending_bytes.size()) ? e.pending_bytes[i] : 0.0;
-            cudaEventDestroy(e.pending[i].first);
-            cudaEventDestroy(e.pending[i].second);
+            pool.push_back(e.pending[i].first);
+            pool.push_back(e.pending[i].second);
         }
         e.pending.clear();
         e.pending_bytes.clear();
@@ -96,6 +110,7 @@ Profiler::~Profiler() {
             cudaEventDestroy(p.first);
             cudaEventDestroy(p.second);
         }
+    for (auto ev : pool) cudaEventDestroy(ev);
 }
 
 // ---------------------------------------------------------------------------

@@ -60,7 +60,9 @@ struct KernelProfile {
 struct Profiler {
     bool on = false;
     std::vector<KernelProfile> k;
+    std::vector<cudaEvent_t> pool;  // recycled events (creation is not free)
     cudaStream_t stream = nullptr;
+    cudaEvent_t take();
     int begin(const char* name, double bytes, cudaEvent_t* start_out, int* idx);
     void end(int idx, cudaEvent_t start);
     void drain();  // turn pending event pairs into totals (synchronises)
