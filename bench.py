@@ -174,16 +174,101 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_serving(args, rank, world):
+    """Continuous-batching serving of a Poisson stream of mixed solves.
+
+    Requests: volumes uniform in {8^3x16, 16^3x32, 24^3x48}, eps in {0.3, 0.6},
+    bare mass with the left spectral edge at delta ~ log-uniform[1e-3, 1e-2],
+    1-12 Gaussian right-hand sides, tol 1e-10, FP16 SAP storage; arrivals
+    Poisson at --rate req/s (seeded); server budget 150 GB of device memory.
+    """
+    import threading
+
+    import numpy as np
+    import torch
+
+    import fieldgen as fg
+    import paper_1204_5463_gb300 as dw
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(1234 + rank)
+    vols = [(8, 8, 8, 16), (16, 16, 16, 32), (24, 24, 24, 48)]
+    epss = [0.3, 0.6]
+    fields = {(d, e): fg.gauge_field(d, e, seed=0) for d in vols for e in epss}
+    edges = fg.spectral_edges()
+    reqs = []
+    t = 0.0
+    for i in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        d = vols[rng.integers(len(vols))]
+        e = epss[rng.integers(len(epss))]
+        delta = float(np.exp(rng.uniform(np.log(1e-3), np.log(1e-2))))
+        m0 = delta - edges[fg.edge_key(d, e, 0)]["edge_re"]
+        nrhs = int(rng.integers(1, 13))
+        b = np.ascontiguousarray(fg.gaussian_source(d, 5000 + i, nrhs=nrhs))
+        reqs.append(dict(t=t, dims=d, eps=e, m0=m0, delta=delta, nrhs=nrhs, b=b, x=np.zeros_like(b)))
+    srv = dw.dw_server_create(150 << 30, args.slots)
+    keep = []
+    ids = [None] * len(reqs)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, q in enumerate(reqs):
+            dt = q["t"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            P = dw.dw_default_params(m=30, k=10, tol=1e-10, sap_cycles=5, mr_steps=4, sap_prec=dw.DW_F16,
+                                     nrhs=q["nrhs"])
+            r = dw.make_request(q["dims"], (4, 4, 4, 4), q["m0"], fields[(q["dims"], q["eps"])], q["b"], q["x"], P)
+            keep.append(r)
+            ids[i] = dw.dw_server_submit(srv, r)
+
+    t_start = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat, ok, solved = [], 0, 0
+    for i, q in enumerate(reqs):
+        status, S, l = dw.dw_server_wait(srv, ids[i], 3600)
+        lat.append(l)
+        ok += status == dw.DW_OK
+        solved += S.converged
+    wall = time.perf_counter() - t_start
+    info = dw.dw_server_info(srv)
+    dw.dw_server_destroy(srv)
+    line = {
+        "metric": "served SAP-FGMRES-DR solves/s (continuous batching, HBM budget 150 GB)",
+        "value": solved / wall, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+        "requests": len(reqs), "requests_ok": ok, "rhs_solved": solved,
+        "offered_req_per_s": args.rate, "achieved_req_per_s": len(reqs) / wall, "wall_s": wall,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(max(lat))},
+        "peak_hbm_gb": info["peak_bytes"] / 1e9, "slots": args.slots, "dtype": "f16 SAP + f32 D z / f64 outer",
+        "data": "synthetic",
+        "config": {"workload": "serving: volumes {8^3x16,16^3x32,24^3x48}, eps {0.3,0.6}, "
+                               "min|lambda| log-uniform [1e-3,1e-2], 1-12 rhs, tol 1e-10, m 30, k 10, SAP 5x4"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-iterations", type=int, default=60,
-                    help="Arnoldi steps per solve used to scale the reference sample")
+    ap.add_argument("--ref-iterations", type=int, default=81,
+                    help="Arnoldi steps per solve used to scale the reference sample (the GPU solver's count on "
+                         "this workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sap-prec", default="f32")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the serving measurement instead")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--slots", type=int, default=8)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -199,6 +284,8 @@ def main():
 
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.serving:
+        return run_serving(args, rank, world)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)
         if dist:
@@ -286,6 +373,36 @@ def main():
         e2e_s = float(t.item())
     e2e_value = args.steps * world / e2e_s
 
+    # the same lattice, 12 right-hand sides per launch, FP16 SAP storage: the
+    # mixed-precision batched solver against the plain single-rhs one above
+    mb = None
+    if not args.no_batched:
+        b12 = fg.gaussian_source(dims, 100 + rank, nrhs=12)
+        b12d = dev(b12)
+        x12d = torch.zeros_like(b12d)
+        P12 = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                                   mr_steps=cfg["mr_steps"], sap_prec=dw.DW_F16, matvec_prec=dw.DW_F32, nrhs=12)
+        S12 = dw.fgmresdr_solve(ctx, b12d, x12d, P12)
+        barrier()
+        m0e, m1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0e.record(stream)
+        nb_steps = max(1, args.steps // 2)
+        for _ in range(nb_steps):
+            S12 = dw.fgmresdr_solve(ctx, b12d, x12d, P12)
+            assert S12.converged == 12
+        m1e.record(stream)
+        barrier()
+        mms = m0e.elapsed_time(m1e)
+        if dist:
+            t = torch.tensor([mms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mms = float(t.item())
+        mb_value = 12 * nb_steps * world / (mms / 1e3)
+        mb = {"value": mb_value, "unit": "solves/s", "nrhs": 12, "sap_prec": "f16", "steps": nb_steps,
+              "ms_per_step": mms / nb_steps, "iterations_max": S12.iterations,
+              "true_rel_res_max": max(S12.true_rel_res[i] for i in range(12)), "ratio_vs_plain": mb_value / value}
+        del b12d, x12d
+
     # roofline of the dominant kernel class of the step
     peaks, peak_src = measured_peaks()
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
@@ -320,6 +437,7 @@ def main():
                 "d2h_bytes_per_step": int(xh.numel() * 8)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "mixed_batched": mb,
     }
     if rank == 0 and not args.no_cpu_baseline:
         t_it, n = oracle_sample(cfg, U, b, 3)

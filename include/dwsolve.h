@@ -175,6 +175,51 @@ long long dw_kernel_launches(void);
 /* Copies up to max entries into out, sets *n; reset != 0 clears the totals. */
 int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset);
 
+/* ---- serving ----------------------------------------------------------------
+ * A solve server admits requests of any lattice, mass, gauge field and
+ * right-hand-side count while their estimated device memory
+ * (dw_request_bytes) fits the budget and one of max_slots slots is free;
+ * queued requests are taken first-in first-out, and a later request that fits
+ * may start while an earlier one waits for memory. Each admitted request runs
+ * fgmresdr_solve on its own CUDA stream and context, so concurrent requests
+ * overlap on the device. Not part of the paper: this is the request loop the
+ * solver is deployed behind. */
+typedef struct {
+    dw_lattice lattice;      /* dims, domain block, m0                                     */
+    const double* U;         /* host, canonical gauge field; valid until the request is done */
+    const double* b;         /* host, params.nrhs canonical spinor fields                   */
+    double* x;               /* host, params.nrhs canonical spinor fields (output)          */
+    dw_solver_params params; /* host_buffers is forced to 1, use_x0 applies to x           */
+} dw_request;
+
+typedef struct {
+    size_t budget_bytes, in_use_bytes, peak_bytes;
+    int running, queued;
+    long long completed;
+} dw_server_status;
+
+typedef struct dw_server dw_server;
+
+/* Estimated device bytes of a request: gauge copies (FP64 + FP32 [+ SAP
+ * storage]) + upload staging + per rhs ((m+1) outer vectors + m SAP-storage
+ * vectors + x, b, r + SAP input + host staging) + k rotation scratch. */
+size_t dw_request_bytes(const dw_request* r);
+
+/* Creates the server on the current device with max_slots worker threads. */
+int dw_server_create(size_t hbm_budget_bytes, int max_slots, dw_server** out);
+/* Queues a request (returns at once). DW_ENOMEM if it exceeds the whole budget. */
+int dw_server_submit(dw_server* s, const dw_request* r, uint64_t* id);
+/* *done = 1 once finished; then *status (DW_OK, DW_ENOTCONV, DW_ECANCELLED,
+ * ...), *S and the submit-to-done latency are filled (each may be NULL). */
+int dw_server_poll(dw_server* s, uint64_t id, int* done, int* status, dw_stats* S, double* latency_s);
+/* Blocks until the request is done or timeout_s passed (DW_ETIMEOUT). */
+int dw_server_wait(dw_server* s, uint64_t id, double timeout_s, int* status, dw_stats* S, double* latency_s);
+/* Cancels a queued request; running requests are not interrupted. */
+int dw_server_cancel(dw_server* s, uint64_t id);
+int dw_server_info(dw_server* s, dw_server_status* out);
+/* Cancels queued requests, waits for running ones, frees everything. */
+void dw_server_destroy(dw_server* s);
+
 #ifdef __cplusplus
 }
 #endif

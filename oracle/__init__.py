@@ -408,6 +408,67 @@ def arnoldi_ritz(apply, n: int, m: int, seed: int = 0):
     return theta, bounds
 
 
+def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int = 40, tol: float = 1e-3,
+                      seed: int = 0):
+    """Leftmost eigenvalue estimate by thick-restarted Arnoldi (Krylov-Schur,
+    Stewart 2002) in bounded memory: m-dimensional bases, restarted on the k
+    Schur vectors of smallest real part, until the leftmost Ritz value's
+    residual bound |h_{m+1,m} z_{m,1}| is below tol. Returns (theta, bound,
+    matvecs)."""
+    import scipy.linalg as sla
+
+    rng = np.random.default_rng(seed)
+    V = np.zeros((m + 1, n), dtype=np.complex128)
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    V[0] = v / np.linalg.norm(v)
+    p = 0
+    matvecs = 0
+    theta = bound = None
+    for _ in range(max_restarts):
+        for j in range(p, m):
+            w = np.asarray(apply(V[j]), dtype=np.complex128)
+            matvecs += 1
+            for _pass in range(2):
+                h = (V[:j + 1] @ w.conj()).conj()
+                w = w - V[:j + 1].T @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            V[j + 1] = w / H[j + 1, j]
+        lam = np.linalg.eigvals(H[:m, :m])
+        cut = np.sort(lam.real)[k - 1]
+        T, Z, sdim = sla.schur(H[:m, :m], output="complex", sort=lambda x: x.real <= cut)
+        kk = max(1, min(sdim, m - 1))
+        ritz = np.diagonal(T)[:kk]
+        bounds = np.abs(H[m, m - 1] * Z[m - 1, :kk])
+        i = int(np.argmin(ritz.real))
+        theta, bound = ritz[i], bounds[i]
+        if bound < tol:
+            break
+        # truncate to the selected Schur vectors and restart
+        Vk = Z[:, :kk].T @ V[:m]
+        hrow = H[m, m - 1] * Z[m - 1, :kk]
+        vlast = V[m].copy()
+        V[:] = 0
+        H[:] = 0
+        V[:kk] = Vk
+        V[kk] = vlast
+        H[:kk, :kk] = T[:kk, :kk]
+        H[kk, :kk] = hrow
+        p = kk
+    return theta, bound, matvecs
+
+
+def tune_m0_schur(U, dims, target: float, m: int = 60, k: int = 20, tol: float = 1e-3, seed: int = 0):
+    """As tune_m0_arnoldi with a thick-restarted Arnoldi (bounded memory)."""
+    V = int(np.prod(dims))
+    U = _cvec(U)
+    t0 = time.time()
+    theta, bound, mv = krylov_schur_edge(
+        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0).reshape(-1), 12 * V, m, k, tol=tol, seed=seed)
+    return target - theta.real, theta, bound, mv, time.time() - t0
+
+
 def tune_m0_arnoldi(U, dims, target: float, m: int = 200, seed: int = 0):
     """Bare mass from the leftmost Ritz value of D at m0 = 0.
 

@@ -46,6 +46,16 @@ class dw_stats(ctypes.Structure):
                 ("time_s", ctypes.c_double)]
 
 
+class dw_request(ctypes.Structure):
+    _fields_ = [("lattice", dw_lattice), ("U", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("params", dw_solver_params)]
+
+
+class dw_server_status(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("running", ctypes.c_int), ("queued", ctypes.c_int), ("completed", ctypes.c_longlong)]
+
+
 class dw_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -66,6 +76,16 @@ _SIGS = {
     "dw_profile": ([_P, _I], _I),
     "dw_kernel_launches": ([], ctypes.c_longlong),
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
+    "dw_request_bytes": ([ctypes.POINTER(dw_request)], ctypes.c_size_t),
+    "dw_server_create": ([ctypes.c_size_t, _I, ctypes.POINTER(_P)], _I),
+    "dw_server_submit": ([_P, ctypes.POINTER(dw_request), ctypes.POINTER(ctypes.c_uint64)], _I),
+    "dw_server_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(dw_stats),
+                        ctypes.POINTER(ctypes.c_double)], _I),
+    "dw_server_wait": ([_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_I), ctypes.POINTER(dw_stats),
+                        ctypes.POINTER(ctypes.c_double)], _I),
+    "dw_server_cancel": ([_P, ctypes.c_uint64], _I),
+    "dw_server_info": ([_P, ctypes.POINTER(dw_server_status)], _I),
+    "dw_server_destroy": ([_P], None),
     "dw_dense_eig": ([_I, _P, _P, _P], _I),
     "dw_dense_qr": ([_I, _I, _P, _P, _P], _I),
     "dw_dense_lstsq": ([_I, _I, _I, _P, _P, _P, _P], _I),
@@ -170,6 +190,58 @@ def dw_profile_read(ctx, reset: bool = False) -> dict:
     _check(_lib.dw_profile_read(ctx, buf, 64, ctypes.byref(n), int(bool(reset))), "dw_profile_read")
     return {buf[i].name.decode(): dict(launches=buf[i].launches, total_ms=buf[i].total_ms, bytes=buf[i].bytes)
             for i in range(min(n.value, 64))}
+
+
+def make_request(dims, block, m0, U, b, x, params: dw_solver_params) -> dw_request:
+    """A request over host buffers (numpy arrays kept alive by the caller)."""
+    L = dw_lattice((ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(*block), float(m0))
+    return dw_request(L, _ptr(U), _ptr(b), _ptr(x), params)
+
+
+def dw_request_bytes(req: dw_request) -> int:
+    return int(_lib.dw_request_bytes(ctypes.byref(req)))
+
+
+def dw_server_create(hbm_budget_bytes: int, max_slots: int) -> int:
+    h = _P()
+    _check(_lib.dw_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)), "dw_server_create")
+    return h.value
+
+
+def dw_server_submit(server, req: dw_request) -> int:
+    rid = ctypes.c_uint64()
+    _check(_lib.dw_server_submit(server, ctypes.byref(req), ctypes.byref(rid)), "dw_server_submit")
+    return rid.value
+
+
+def dw_server_poll(server, rid: int):
+    done, status, lat = _I(), _I(), ctypes.c_double()
+    S = dw_stats()
+    _check(_lib.dw_server_poll(server, int(rid), ctypes.byref(done), ctypes.byref(status), ctypes.byref(S),
+                               ctypes.byref(lat)), "dw_server_poll")
+    return bool(done.value), status.value, S, lat.value
+
+
+def dw_server_wait(server, rid: int, timeout_s: float = 600.0):
+    status, lat = _I(), ctypes.c_double()
+    S = dw_stats()
+    _check(_lib.dw_server_wait(server, int(rid), float(timeout_s), ctypes.byref(status), ctypes.byref(S),
+                               ctypes.byref(lat)), "dw_server_wait")
+    return status.value, S, lat.value
+
+
+def dw_server_cancel(server, rid: int) -> None:
+    _check(_lib.dw_server_cancel(server, int(rid)), "dw_server_cancel")
+
+
+def dw_server_info(server) -> dict:
+    st = dw_server_status()
+    _check(_lib.dw_server_info(server, ctypes.byref(st)), "dw_server_info")
+    return {f: getattr(st, f) for f, _ in dw_server_status._fields_}
+
+
+def dw_server_destroy(server) -> None:
+    _lib.dw_server_destroy(server)
 
 
 def dw_dense_eig(n: int, A, lam, vecs) -> None:

@@ -25,7 +25,7 @@ int DevBuf::ensure(size_t n) {
     if (n <= bytes && p) return DW_OK;
     release();
     if (n == 0) return DW_OK;
-    cudaError_t e = cudaMalloc(&p, n);
+    cudaError_t e = cudaMallocAsync(&p, n, st);
     if (e != cudaSuccess) {
         p = nullptr;
         bytes = 0;
@@ -38,7 +38,7 @@ int DevBuf::ensure(size_t n) {
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     bytes = 0;
 }
@@ -174,6 +174,7 @@ int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out) {
         return fail(DW_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
     c->sap_threads.assign(4, 0);
+    for (auto* b : {&c->U[0], &c->U[1], &c->U[2], &c->U[3], &c->work_in, &c->work_out, &c->work_aux}) b->st = c->stream;
     *out = c;
     return DW_OK;
 }
@@ -182,7 +183,9 @@ void dw_destroy(dw_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     release_workspace(ctx->ws);
+    cudaStream_t st = ctx->stream;
     delete ctx;
+    cudaStreamSynchronize(st);  // the stream-ordered frees have completed
 }
 
 int dw_set_mass(dw_ctx* ctx, double m0) {

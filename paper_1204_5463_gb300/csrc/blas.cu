@@ -223,20 +223,24 @@ __global__ void __launch_bounds__(kMD, 1) multidot_kernel(VecRef Vb, VecRef w, l
     for (int i = nv + t; i < nvmax; i += kMD) out[i] = make_double2(0.0, 0.0);
 }
 
-// out[r][i] = sum_blk partial[r][blk][i] in fixed order
-__global__ void __launch_bounds__(kT) finalize_kernel(const double2* partial, int nblk, int NP, const int* jtab,
-                                                      double2* out) {
+// out[r][i] = sum_blk partial[r][blk][i]: warp i sums its row lane-strided,
+// then a fixed shuffle tree (deterministic)
+__global__ void __launch_bounds__(1024) finalize_kernel(const double2* partial, int nblk, int NP, const int* jtab,
+                                                        double2* out) {
     const int r = blockIdx.x;
     if (jtab && jtab[r] < 0) return;
-    for (int i = threadIdx.x; i < NP; i += kT) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < NP; i += 32) {
         double2 s = make_double2(0.0, 0.0);
         const double2* p = partial + (long long)r * nblk * NP + i;
-        for (int b = 0; b < nblk; ++b) {
+        for (int b = lane; b < nblk; b += 32) {
             const double2 t = p[(long long)b * NP];
             s.x += t.x;
             s.y += t.y;
         }
-        out[(long long)r * NP + i] = s;
+        s.x = warp_sum(s.x);
+        s.y = warp_sum(s.y);
+        if (lane == 0) out[(long long)r * NP + i] = s;
     }
 }
 
@@ -521,7 +525,7 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
     else
         multidot_kernel<P64><<<dim3((unsigned)nb, nrhs), kMD, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
     DW_LAUNCH_CHECK();
-    finalize_kernel<<<nrhs, kT, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
+    finalize_kernel<<<nrhs, 1024, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
     DW_LAUNCH_CHECK();
     return DW_OK;
 }

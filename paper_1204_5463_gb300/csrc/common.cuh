@@ -15,7 +15,7 @@ namespace dwk {
 // complex numbers
 // ---------------------------------------------------------------------------
 template <class R>
-struct cx {
+struct __align__(2 * sizeof(R)) cx {
     R re, im;
 };
 

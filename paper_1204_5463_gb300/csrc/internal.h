@@ -39,6 +39,7 @@ void count_launch();
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t st = nullptr;  // allocations are stream-ordered on the owner's stream
     int ensure(size_t n);
     void release();
     template <class T>

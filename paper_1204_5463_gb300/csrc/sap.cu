@@ -13,6 +13,9 @@
 //   4. writes x^l + y^l back.
 // Domains of one colour never couple (even domain count per direction), so
 // all CTAs of a launch are independent and the launch order is irrelevant.
+#include <mutex>
+#include <set>
+
 #include "internal.h"
 
 namespace dwk {
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     typedef typename link_word<PL>::type LW;
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x;
-    C* rho_sh = reinterpret_cast<C*>(smem);                                   // [24][T]
+    cx<C>* rho_sh = reinterpret_cast<cx<C>*>(smem);                           // [12][T] complex
     LW* link_sh = reinterpret_cast<LW*>(smem + sizeof(C) * 24 * T);          // [4][9][T]
     C* red = reinterpret_cast<C*>(smem + sizeof(C) * 24 * T + sizeof(LW) * 36 * T);  // [32][3]
 
@@ -104,14 +107,24 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     for (int j = 0; j < 4; ++j) xg[j] = D[j] * g.b[j] + lx[j];
     const long long s = site_index(g, xg);
 
-    // 1. own links -> shared memory (raw storage words)
+    // 1. own links -> shared memory (raw storage words); in the general mode
+    //    also the domain's own iterate x (read by interior hops of the residual)
+    const char* lsh = reinterpret_cast<const char*>(link_sh);
     if (act) {
         const LW* Ug = reinterpret_cast<const LW*>(U);
 #pragma unroll 4
         for (int c = 0; c < 36; ++c) link_sh[c * T + tid] = Ug[(long long)c * g.V + s];
+        if (mode == 2) {
+            cx<C> xo[12];
+            load_spinor<PS, C>(xb, g.V, s, xo);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) rho_sh[c * T + tid] = xo[c];
+        }
     }
+    __syncthreads();
 
-    // 2. residual r = v - D x at this site
+    // 2. residual r = v - D x at this site: interior neighbours and every
+    //    forward link from shared memory, boundary neighbours through L2
     cx<C> rho[12], y[12];
     if (act) {
         load_spinor<PS, C>(vb, g.V, s, rho);
@@ -119,17 +132,29 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             cx<C> acc[12], psi[12], u[9];
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[c] = czero<C>();
-            const bool own_zero = (mode == 1);
+            const bool general = (mode == 2);
 #define SAP_RES_HOPS(MU)                                                                     \
     {                                                                                        \
-        const bool in_p = lx[MU] + 1 < g.b[MU];                                              \
-        if (!(own_zero && in_p)) {                                                           \
+        if (lx[MU] + 1 < g.b[MU]) {                                                          \
+            if (general) {                                                                   \
+                const int tn = tid + lstride[MU];                                            \
+                _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];  \
+                load_link<PL, C, false>(lsh, T, MU, tid, u);                                 \
+                hop<MU, +1, C>(psi, u, acc);                                                 \
+            }                                                                                \
+        } else {                                                                             \
             load_spinor<PS, C>(xb, g.V, neighbour(g, s, xg, MU, +1), psi);                   \
-            load_link<PL, C>(U, g.V, MU, s, u);                                              \
+            load_link<PL, C, false>(lsh, T, MU, tid, u);                                     \
             hop<MU, +1, C>(psi, u, acc);                                                     \
         }                                                                                    \
-        const bool in_m = lx[MU] >= 1;                                                       \
-        if (!(own_zero && in_m)) {                                                           \
+        if (lx[MU] >= 1) {                                                                   \
+            if (general) {                                                                   \
+                const int tn = tid - lstride[MU];                                            \
+                _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];  \
+                load_link<PL, C, false>(lsh, T, MU, tn, u);                                  \
+                hop<MU, -1, C>(psi, u, acc);                                                 \
+            }                                                                                \
+        } else {                                                                             \
             const long long sm = neighbour(g, s, xg, MU, -1);                                \
             load_spinor<PS, C>(xb, g.V, sm, psi);                                            \
             load_link<PL, C>(U, g.V, MU, sm, u);                                             \
@@ -142,10 +167,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             SAP_RES_HOPS(3)
 #undef SAP_RES_HOPS
             const C half = (C)0.5;
-            if (!own_zero) {
-                load_spinor<PS, C>(xb, g.V, s, psi);
+            if (general) {
 #pragma unroll
-                for (int c = 0; c < 12; ++c) rho[c] = rho[c] - (diag * psi[c] - half * acc[c]);
+                for (int c = 0; c < 12; ++c) rho[c] = rho[c] - (diag * rho_sh[c * T + tid] - half * acc[c]);
             } else {
 #pragma unroll
                 for (int c = 0; c < 12; ++c) rho[c] = rho[c] + half * acc[c];
@@ -157,15 +181,12 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     }
 #pragma unroll
     for (int c = 0; c < 12; ++c) y[c] = czero<C>();
+    __syncthreads();  // x in shared memory is overwritten by the MR iterate below
 
     // 3. MR on D^l y = r^l out of shared memory
-    const char* lsh = reinterpret_cast<const char*>(link_sh);
     for (int it = 0; it < nmr; ++it) {
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            rho_sh[(2 * c) * T + tid] = rho[c].re;
-            rho_sh[(2 * c + 1) * T + tid] = rho[c].im;
-        }
+        for (int c = 0; c < 12; ++c) rho_sh[c * T + tid] = rho[c];
         __syncthreads();
         cx<C> p[12];
         C pr_re = 0, pr_im = 0, pp = 0;
@@ -177,15 +198,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     {                                                                                         \
         if (lx[MU] + 1 < g.b[MU]) {                                                           \
             const int tn = tid + lstride[MU];                                                 \
-            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] =                           \
-                mk<C>(rho_sh[(2 * c) * T + tn], rho_sh[(2 * c + 1) * T + tn]);                \
+            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];       \
             load_link<PL, C, false>(lsh, T, MU, tid, u);                                      \
             hop<MU, +1, C>(psi, u, acc);                                                      \
         }                                                                                     \
         if (lx[MU] >= 1) {                                                                    \
             const int tn = tid - lstride[MU];                                                 \
-            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] =                           \
-                mk<C>(rho_sh[(2 * c) * T + tn], rho_sh[(2 * c + 1) * T + tn]);                \
+            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];       \
             load_link<PL, C, false>(lsh, T, MU, tn, u);                                       \
             hop<MU, -1, C>(psi, u, acc);                                                      \
         }                                                                                     \
@@ -237,13 +256,20 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
                  int colour, int nmr, int mode, int threads, cudaStream_t st) {
     typedef typename link_word<PL>::type LW;
     const size_t smem = sizeof(C) * 24 * threads + sizeof(LW) * 36 * threads + sizeof(C) * 3 * 32;
-    static bool attr_set = false;  // benign race: the attribute value is the same for every caller
-    if (!attr_set) {
-        DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 256>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 1024>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr_set = true;
+    // the shared-memory limit is a per-device property of the kernel: set it once per device
+    static std::mutex mu;
+    static std::set<int> done;
+    {
+        int dev = 0;
+        DW_CUDA_TRY(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done.count(dev)) {
+            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 256>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 1024>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            done.insert(dev);
+        }
     }
     const unsigned nb = (unsigned)(g.ndom / 2) * (unsigned)nrhs;
     if (threads <= 256)

@@ -115,7 +115,14 @@ struct Workspace {
 void release_workspace(Workspace* w) { delete w; }
 
 static Workspace* workspace_of(dw_ctx* ctx) {
-    if (!ctx->ws) ctx->ws = new (std::nothrow) Workspace();
+    if (!ctx->ws) {
+        ctx->ws = new (std::nothrow) Workspace();
+        if (ctx->ws)
+            for (DevBuf* b : {&ctx->ws->V, &ctx->ws->Z, &ctx->ws->x, &ctx->ws->b, &ctx->ws->r, &ctx->ws->vlow,
+                              &ctx->ws->zscr, &ctx->ws->partial, &ctx->ws->dots, &ctx->ws->Q, &ctx->ws->eta,
+                              &ctx->ws->norm2, &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon})
+                b->st = ctx->stream;
+    }
     return ctx->ws;
 }
 

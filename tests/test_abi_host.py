@@ -133,3 +133,16 @@ def test_dense_solve(dw):
     x = b.copy()
     dw.dw_dense_solve(30, A, x)
     assert np.linalg.norm(A @ x - b) < 1e-12 * np.linalg.norm(b)
+
+
+def test_request_bytes_formula(dw):
+    """Admission estimate: gauge copies + staging + per-rhs Krylov workspace."""
+    P = dw.dw_default_params(m=30, k=10, nrhs=3, sap_prec=dw.DW_F16)
+    dims = (16, 16, 16, 32)
+    V = 16 * 16 * 16 * 32
+    req = dw.make_request(dims, (4, 4, 4, 4), -0.6, 1, 1, 1, P)
+    sb = 52 * V
+    gauge = 576 * V + 576 * V + 288 * V + 144 * V
+    per_rhs = 31 * 192 * V + 30 * sb + 3 * 192 * V + sb + 24 * 8 * V
+    expect = gauge + 3 * per_rhs + 10 * sb + (8 << 20)
+    assert dw.dw_request_bytes(req) == expect
