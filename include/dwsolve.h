@@ -175,6 +175,29 @@ long long dw_kernel_launches(void);
 /* Copies up to max entries into out, sets *n; reset != 0 clears the totals. */
 int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset);
 
+/* ---- allocation-free operator ----------------------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot call cudaMalloc (code inside a pre-reserved memory pool, allocators
+ * that forbid device allocation, processes with a fixed memory budget).
+ *
+ * out = D in with FP32 storage and arithmetic, exactly as dw_apply(..., DW_F32,
+ * 1) computes it, but without a context and without allocating anything: the
+ * FP32 copies of the links and of the fields live in one file-scope device
+ * array of 2 MiB (480 bytes per site), so the lattice may have at most 4096
+ * sites (larger lattices return DW_EINVAL). dims: the four extents (no domain
+ * decomposition is needed); U: device pointer, canonical FP64 gauge field
+ * (V*72 doubles); in, out: device pointers, one canonical FP64 spinor field
+ * each (V*24 doubles); cuda_stream: cudaStream_t or NULL. Returns after the
+ * work on the stream has completed.
+ * The first call on a device looks up the array's device address (set-up, once
+ * per device); make that first call before any stream capture. Every call
+ * overwrites the whole part of the array it reads, so nothing needs clearing,
+ * but all calls share the array: calls that overlap on the GPU (other threads
+ * or streams) race and must be serialised by the caller. Every GPU that loads
+ * the library holds the 2 MiB until the process exits. */
+int dw_apply_f32_noalloc(const int* dims, double m0, const double* U, const double* in, double* out,
+                         void* cuda_stream);
+
 /* ---- serving ----------------------------------------------------------------
  * A solve server admits requests of any lattice, mass, gauge field and
  * right-hand-side count while their estimated device memory

@@ -76,6 +76,7 @@ _SIGS = {
     "dw_profile": ([_P, _I], _I),
     "dw_kernel_launches": ([], ctypes.c_longlong),
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
+    "dw_apply_f32_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_double, _P, _P, _P, _P], _I),
     "dw_request_bytes": ([ctypes.POINTER(dw_request)], ctypes.c_size_t),
     "dw_server_create": ([ctypes.c_size_t, _I, ctypes.POINTER(_P)], _I),
     "dw_server_submit": ([_P, ctypes.POINTER(dw_request), ctypes.POINTER(ctypes.c_uint64)], _I),
@@ -190,6 +191,13 @@ def dw_profile_read(ctx, reset: bool = False) -> dict:
     _check(_lib.dw_profile_read(ctx, buf, 64, ctypes.byref(n), int(bool(reset))), "dw_profile_read")
     return {buf[i].name.decode(): dict(launches=buf[i].launches, total_ms=buf[i].total_ms, bytes=buf[i].bytes)
             for i in range(min(n.value, 64))}
+
+
+def dw_apply_f32_noalloc(dims, m0: float, U, inp, out, stream=None) -> None:
+    """out = D in (FP32) without any device allocation (lattices up to 4096 sites)."""
+    d = (ctypes.c_int * 4)(*dims)
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(_lib.dw_apply_f32_noalloc(d, float(m0), _ptr(U), _ptr(inp), _ptr(out), s), "dw_apply_f32_noalloc")
 
 
 def make_request(dims, block, m0, U, b, x, params: dw_solver_params) -> dw_request:
