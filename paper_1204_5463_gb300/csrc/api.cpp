@@ -116,7 +116,7 @@ Profiler::~Profiler() {
 // ---------------------------------------------------------------------------
 int gauge_for(dw_ctx* ctx, int prec, const char** out) {
     if (!ctx->have_gauge) return fail(DW_EINVAL, "gauge field not set");
-    if (prec < 0 || prec > 3) return fail(DW_EINVAL, "bad precision");
+    if (prec < 0 || prec > 4) return fail(DW_EINVAL, "bad precision");
     if (!ctx->U_ready[prec]) {
         int rc = ctx->U[prec].ensure((size_t)link_bytes(prec, ctx->g.V));
         if (rc) return rc;
@@ -174,7 +174,8 @@ int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out) {
         return fail(DW_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
     c->sap_threads.assign(4, 0);
-    for (auto* b : {&c->U[0], &c->U[1], &c->U[2], &c->U[3], &c->work_in, &c->work_out, &c->work_aux}) b->st = c->stream;
+    for (auto* b : {&c->U[0], &c->U[1], &c->U[2], &c->U[3], &c->U[4], &c->work_in, &c->work_out, &c->work_aux})
+        b->st = c->stream;
     *out = c;
     return DW_OK;
 }
@@ -206,7 +207,7 @@ int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device) {
         src = ctx->work_aux.as<double>();
     }
     if ((rc = launch_gauge_convert(P64, src, ctx->U[P64].as<char>(), ctx->g.V, ctx->stream))) return rc;
-    for (int p = 0; p < 4; ++p) ctx->U_ready[p] = false;
+    for (int p = 0; p < 5; ++p) ctx->U_ready[p] = false;
     ctx->U_ready[P64] = true;
     ctx->have_gauge = true;
     DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));

@@ -18,7 +18,6 @@ namespace dwk {
 namespace {
 
 constexpr int kT = 256;      // threads per CTA
-constexpr int kGroup = 8;    // basis vectors per sweep of a multi-dot
 constexpr int kRotMax = 17;  // output columns held in registers by a rotation
 constexpr int kMaxV = 64;    // basis vectors per multi-dot / multi-axpy
 
@@ -129,98 +128,99 @@ struct Elem<PDF> {
 // i = q, q + 8, q + 16, ... and sweeps them over the chunk with its lanes, so
 // every V_i element is read once, coalesced, and the warp reductions happen
 // once per CTA at the end.
-constexpr int kChunk = 2048;
-constexpr int kMD = 1024;  // threads per multi-dot CTA: 32 warps, at most 2 vectors per warp
+constexpr int kDotE = 16;              // elements per thread per range
+constexpr int kDotG = 8;               // basis vectors per CTA
+constexpr int kDotRange = kT * kDotE;  // elements per range (4096)
 
+// partial[r][blk][i] over the ranges this CTA sweeps, for its group of 8
+// vectors; the CTAs of group 0 also write ||w||^2 and zero the unused slots.
 template <int VP>
-__global__ void __launch_bounds__(kMD, 1) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
-                                                          int nv_off, int nvmax, double2* partial) {
+__global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
+                                                         int nv_off, int nvmax, int ngroups, double2* partial) {
     typedef Elem<VP> E;
     typedef typename E::C C;
     typedef typename E::T T16;
-    __shared__ T16 ws[kChunk];
-    __shared__ double red[kMD / 32];
+    __shared__ T16 ws[kDotRange];
+    __shared__ double2 red[kDotG][kT / 32];
+    __shared__ double redn[kT / 32];
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
     const int nv = rhs_nv(jtab, r, nv_off);
     const int j = jtab ? jtab[r] : 0;
+    const int grp = blockIdx.x % ngroups;
+    const int slot = blockIdx.x / ngroups;  // partial slot of this CTA
+    const int nslots = gridDim.x / ngroups;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int NW = kMD / 32;
-    const double2* Vr = Vb.base + r * Vb.rhs_stride + (long long)Vb.col_off * Vb.col_stride;
+    const int i0 = grp * kDotG;
+    const int G = max(0, min(kDotG, nv - i0));  // vectors of this CTA
+    const double2* Vr = Vb.base + r * Vb.rhs_stride + (long long)(Vb.col_off + i0) * Vb.col_stride;
     const T16* wr = reinterpret_cast<const T16*>(w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride);
-    const int R = (nv > warp) ? (nv - warp + NW - 1) / NW : 0;  // vectors of this warp (<= 2)
-    const double2* v0 = Vr + (long long)warp * Vb.col_stride;
-    const double2* v1 = Vr + (long long)(warp + NW) * Vb.col_stride;
-    C a0 = E::zero(), a1 = E::zero();
+    C acc[kDotG];
+#pragma unroll
+    for (int q = 0; q < kDotG; ++q) acc[q] = E::zero();
     typename E::N wacc = E::nzero();
-    for (long long c0 = (long long)blockIdx.x * kChunk; c0 < n; c0 += (long long)gridDim.x * kChunk) {
-        const int cn = (int)min((long long)kChunk, n - c0);
-        __syncthreads();  // the previous chunk is no longer read
-        for (int k = t; k < kChunk; k += kMD) {
-            T16 v;
-            if (k < cn) {
-                v = wr[c0 + k];
-                E::norm2_acc(wacc, E::load_rw(reinterpret_cast<const double2*>(&v), 0));
-            } else {
-                v = T16{};
+    const long long nranges = (n + kDotRange - 1) / kDotRange;
+    for (long long rg = slot; rg < nranges; rg += nslots) {
+        const long long e0 = rg * kDotRange;
+        __syncthreads();  // the previous range of w is no longer read
+#pragma unroll
+        for (int k = 0; k < kDotE; ++k) {
+            const long long e = e0 + t + (long long)k * kT;
+            T16 v{};
+            if (e < n) {
+                v = wr[e];
+                if (grp == 0) E::norm2_acc(wacc, E::load_rw(reinterpret_cast<const double2*>(&v), 0));
             }
-            ws[k] = v;
+            ws[t + k * kT] = v;
         }
         __syncthreads();
-        if (R == 0) continue;
-        int k = lane;
-        for (; k + 96 < cn; k += 128) {  // four elements per lane in flight
-            C x0 = E::load(v0, c0 + k), x1 = E::load(v0, c0 + k + 32), x2 = E::load(v0, c0 + k + 64),
-              x3 = E::load(v0, c0 + k + 96);
-            C y0, y1, y2, y3;
-            if (R > 1) {
-                y0 = E::load(v1, c0 + k);
-                y1 = E::load(v1, c0 + k + 32);
-                y2 = E::load(v1, c0 + k + 64);
-                y3 = E::load(v1, c0 + k + 96);
-            }
-            T16 r0 = ws[k], r1 = ws[k + 32], r2 = ws[k + 64], r3 = ws[k + 96];
-            const C w0 = E::load_rw(reinterpret_cast<const double2*>(&r0), 0);
-            const C w1 = E::load_rw(reinterpret_cast<const double2*>(&r1), 0);
-            const C w2 = E::load_rw(reinterpret_cast<const double2*>(&r2), 0);
-            const C w3 = E::load_rw(reinterpret_cast<const double2*>(&r3), 0);
-            E::mac_conj(a0, x0, w0);
-            E::mac_conj(a0, x1, w1);
-            E::mac_conj(a0, x2, w2);
-            E::mac_conj(a0, x3, w3);
-            if (R > 1) {
-                E::mac_conj(a1, y0, w0);
-                E::mac_conj(a1, y1, w1);
-                E::mac_conj(a1, y2, w2);
-                E::mac_conj(a1, y3, w3);
+        const bool full = e0 + kDotRange <= n;
+        // element-outer, vector-inner: the G accumulators are independent
+        // dependency chains, and the G loads of one element are in flight together
+#pragma unroll 2
+        for (int k = 0; k < kDotE; ++k) {
+            const long long e = e0 + t + (long long)k * kT;
+            const T16 wraw = ws[t + k * kT];
+            const C wv = E::load_rw(reinterpret_cast<const double2*>(&wraw), 0);
+            if (full || e < n) {
+                C vv[kDotG];
+#pragma unroll
+                for (int q = 0; q < kDotG; ++q)
+                    if (q < G) vv[q] = E::load(Vr + (long long)q * Vb.col_stride, e);
+#pragma unroll
+                for (int q = 0; q < kDotG; ++q)
+                    if (q < G) E::mac_conj(acc[q], vv[q], wv);
             }
         }
-        for (; k < cn; k += 32) {
-            T16 rr = ws[k];
-            const C wv = E::load_rw(reinterpret_cast<const double2*>(&rr), 0);
-            E::mac_conj(a0, E::load(v0, c0 + k), wv);
-            if (R > 1) E::mac_conj(a1, E::load(v1, c0 + k), wv);
+    }
+    // CTA reduction of the G dot products (warp shuffles, then across warps)
+#pragma unroll
+    for (int q = 0; q < kDotG; ++q)
+        if (q < G) {
+            const C sq = E::warp_reduce(acc[q]);
+            if (lane == 0) red[q][warp] = E::to_d2(sq);
         }
-    }
-    const int NP = nvmax + 1;
-    double2* out = partial + ((long long)r * gridDim.x + blockIdx.x) * NP;
-    if (R > 0) {
-        const C s0 = E::warp_reduce(a0);
-        if (lane == 0) out[warp] = E::to_d2(s0);
-    }
-    if (R > 1) {
-        const C s1 = E::warp_reduce(a1);
-        if (lane == 0) out[warp + NW] = E::to_d2(s1);
-    }
-    const double wn = warp_sum(E::nfin(wacc));
-    if (lane == 0) red[warp] = wn;
+    const double wn = (grp == 0) ? warp_sum(E::nfin(wacc)) : 0.0;
+    if (lane == 0) redn[warp] = wn;
     __syncthreads();
-    if (t == 0) {
-        double sum = 0.0;
-        for (int q = 0; q < NW; ++q) sum += red[q];
-        out[nvmax] = make_double2(sum, 0.0);
+    const int NP = nvmax + 1;
+    double2* out = partial + ((long long)r * nslots + slot) * NP;
+    if (t < G) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int q = 0; q < kT / 32; ++q) sum.x += red[t][q].x, sum.y += red[t][q].y;
+        out[i0 + t] = sum;
     }
-    for (int i = nv + t; i < nvmax; i += kMD) out[i] = make_double2(0.0, 0.0);
+    if (grp == 0) {
+        if (t == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < kT / 32; ++q) sum += redn[q];
+            out[nvmax] = make_double2(sum, 0.0);
+        }
+        for (int i = t; i < nvmax; i += kT)
+            if (i >= nv || i >= ngroups * kDotG) out[i] = make_double2(0.0, 0.0);
+    } else if (t >= G && t < kDotG && i0 + t < nvmax) {
+        out[i0 + t] = make_double2(0.0, 0.0);
+    }
 }
 
 // out[r][i] = sum_blk partial[r][blk][i]: warp i sums its row lane-strided,
@@ -514,16 +514,18 @@ int blas_nblk(long long n) { return (int)grid_for(n); }
 int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
                     double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
-    if (nvmax > 2 * (kMD / 32)) return fail(DW_EINVAL, "multi-dot handles at most 64 vectors");
     if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
-    // one chunk of w per CTA and sweep, at most three CTAs per SM, never more than partial[] holds
-    long long nb = (n + kChunk - 1) / kChunk;
-    if (nb > 152LL) nb = 152LL;
+    // CTAs: (ranges of w) x (groups of 8 vectors); at most nblk range slots
+    const int ngroups = (nvmax + kDotG - 1) / kDotG;
+    long long nb = (n + kDotRange - 1) / kDotRange;
     if (nb > nblk) nb = nblk;
+    if (nb * ngroups > 152LL * 2 * 8) nb = (152LL * 2 * 8 + ngroups - 1) / ngroups;
+    if (nb < 1) nb = 1;
+    const dim3 grid((unsigned)(nb * ngroups), nrhs);
     if (vp == PDF)
-        multidot_kernel<PDF><<<dim3((unsigned)nb, nrhs), kMD, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
+        multidot_kernel<PDF><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     else
-        multidot_kernel<P64><<<dim3((unsigned)nb, nrhs), kMD, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, partial);
+        multidot_kernel<P64><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     DW_LAUNCH_CHECK();
     finalize_kernel<<<nrhs, 1024, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
     DW_LAUNCH_CHECK();

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dwk {
 
 // ---------------------------------------------------------------------------
@@ -106,7 +108,7 @@ __host__ __device__ inline long long spinor_bytes(int prec, long long V) {
     return (prec == P64 || prec == PDF) ? 192 * V : prec == P32 ? 96 * V : 52 * V;
 }
 __host__ __device__ inline long long link_bytes(int prec, long long V) {
-    return prec == P64 ? 576 * V : prec == P32 ? 288 * V : 144 * V;
+    return (prec == P64 || prec == PDF) ? 576 * V : prec == P32 ? 288 * V : 144 * V;
 }
 
 // ---------------------------------------------------------------------------
@@ -116,6 +118,11 @@ __host__ __device__ inline long long link_bytes(int prec, long long V) {
 // ---------------------------------------------------------------------------
 struct df {
     float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit df(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ explicit df(float v) : hi(v), lo(0.f) {}
+    __host__ __device__ explicit df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
 };
 __device__ __forceinline__ df two_sum(float a, float b) {
     const float s = a + b;
@@ -166,6 +173,12 @@ __device__ __forceinline__ df df_from_double(double x) {
     return df{hi, (float)(x - (double)hi)};
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+// arithmetic operators, so that the stencil templates run in double-float
+__device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df operator-(df a) { return df_neg(a); }
+__device__ __forceinline__ df operator-(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
+
 #ifdef __CUDACC__
 // warp-wide sum of a double-float value (every lane gets the sum)
 __device__ __forceinline__ df df_warp_sum(df a) {
@@ -225,7 +238,14 @@ __device__ __forceinline__ T ld(const T* p) {
 // (G = true: global memory through the read-only path; false: shared memory)
 template <int P, class C, bool G = true>
 __device__ __forceinline__ void load_spinor(const char* base, long long V, long long s, cx<C> out[12]) {
-    if constexpr (P == PDF) {
+    if constexpr (P == PDF && std::is_same<C, df>::value) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            float4 v = ld<float4, G>(&p[c * V + s]);
+            out[c] = mk<C>(df(v.x, v.y), df(v.z, v.w));
+        }
+    } else if constexpr (P == PDF) {
         const float4* p = reinterpret_cast<const float4*>(base);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
@@ -268,7 +288,14 @@ __device__ __forceinline__ void load_spinor(const char* base, long long V, long 
 
 template <int P, class C>
 __device__ __forceinline__ void store_spinor(char* base, long long V, long long s, const cx<C> in[12]) {
-    if constexpr (P == PDF) {
+    if constexpr (P == PDF && std::is_same<C, df>::value) {
+        float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const df a = df_norm(in[c].re), b = df_norm(in[c].im);
+            p[c * V + s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+    } else if constexpr (P == PDF) {
         float4* p = reinterpret_cast<float4*>(base);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
@@ -313,7 +340,14 @@ __device__ __forceinline__ void store_spinor(char* base, long long V, long long 
 // link U_{s,mu} (3x3, row-major) in compute type C
 template <int P, class C, bool G = true>
 __device__ __forceinline__ void load_link(const char* base, long long V, int mu, long long s, cx<C> u[9]) {
-    if constexpr (P == P64) {
+    if constexpr (P == PDF) {  // double-float links (only with the double-float stencil)
+        const float4* p = reinterpret_cast<const float4*>(base) + (long long)mu * 9 * V;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            float4 v = ld<float4, G>(&p[c * V + s]);
+            u[c] = mk<C>(C(v.x, v.y), C(v.z, v.w));
+        }
+    } else if constexpr (P == P64) {
         const double2* p = reinterpret_cast<const double2*>(base) + (long long)mu * 9 * V;
 #pragma unroll
         for (int c = 0; c < 9; ++c) {

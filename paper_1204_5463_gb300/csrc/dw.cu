@@ -75,10 +75,14 @@ __global__ void __launch_bounds__(kThreads) link_convert_kernel(const double2* _
                                                                 long long n) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const double2 t = U[e];
-        if constexpr (P == P32)
+        if constexpr (P == P32) {
             reinterpret_cast<float2*>(out)[e] = make_float2((float)t.x, (float)t.y);
-        else
+        } else if constexpr (P == PDF) {
+            const df a(t.x), b(t.y);
+            reinterpret_cast<float4*>(out)[e] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        } else {
             reinterpret_cast<uint32_t*>(out)[e] = f2_to_h2((float)t.x, (float)t.y, P == PB16);
+        }
     }
 }
 
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) dw_kernel(Geom g, C diag, FieldRef i
     DW_HOPS(3)
 #undef DW_HOPS
     load_spinor<PI, C>(pin, g.V, s, psi);
-    const C half = (C)0.5;
+    const C half = C(0.5f);
     cx<C> res[12];
     if constexpr (SUB) {
         cx<C> b[12];
@@ -146,7 +150,7 @@ template <int PI, int PO, int PL, class C>
 int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const char* U, const int* jtab, int nrhs,
                     const FieldRef* sub, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.V + kThreads - 1) / kThreads) * (unsigned)nrhs;
-    const C diag = (C)(4.0 + m0);
+    const C diag = C(4.0 + m0);
     if (sub) {
         if constexpr (PO == P64 || PO == PDF)
             dw_kernel<PI, PO, PL, C, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, *sub);
@@ -213,6 +217,7 @@ int launch_link_convert(int prec, const char* U64, char* out, long long V, cudaS
         case P32: link_convert_kernel<P32><<<nb, kThreads, 0, st>>>(src, out, n); break;
         case P16: link_convert_kernel<P16><<<nb, kThreads, 0, st>>>(src, out, n); break;
         case PB16: link_convert_kernel<PB16><<<nb, kThreads, 0, st>>>(src, out, n); break;
+        case PDF: link_convert_kernel<PDF><<<nb, kThreads, 0, st>>>(src, out, n); break;
         default: return fail(DW_EINVAL, "bad link precision");
     }
     DW_LAUNCH_CHECK();
@@ -268,6 +273,7 @@ int launch_dw(int pin, int pout, int plink, const Geom& g, double m0, FieldRef i
     DWC(PB16, PDF, P64, double)
     DWC(PDF, PDF, P64, double)
     DWC(P64, PDF, P64, double)
+    DWC(PDF, PDF, PDF, df)
 #undef DWC
     return fail(DW_EINVAL, "unsupported stencil precision combination");
 }

@@ -95,8 +95,8 @@ struct dw_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     bool have_gauge = false;
-    dwk::DevBuf U[4];           // gauge field per storage precision (P64, P32, P16, PB16)
-    bool U_ready[4] = {false, false, false, false};
+    dwk::DevBuf U[5];           // gauge field per storage precision (P64, P32, P16, PB16, PDF)
+    bool U_ready[5] = {false, false, false, false, false};
     dwk::DevBuf work_in, work_out, work_aux;  // conversions in dw_apply / sap_precondition
     dwk::Profiler prof;
     std::vector<int> sap_threads;  // tuned launch shape per precision (0 = default)

@@ -145,7 +145,8 @@ int Solver::setup() {
     int rc;
     if ((rc = gauge_for(ctx, sp, &U_sap))) return rc;
     if ((rc = gauge_for(ctx, mp == P64 ? P64 : P32, &U_mv))) return rc;
-    if ((rc = gauge_for(ctx, P64, &U64))) return rc;
+    // explicit residual: FP64 links for FP64 outer vectors, double-float links otherwise
+    if ((rc = gauge_for(ctx, op == PDF ? PDF : P64, &U64))) return rc;
     Workspace* W = workspace_of(ctx);
     if (!W) return fail(DW_ENOMEM, "workspace allocation failed");
     if ((rc = W->V.ensure((size_t)nrhs * (m + 1) * fb))) return rc;
@@ -359,10 +360,10 @@ int Solver::cycle_end(int r) {
     }
     // explicit FP64 residual r = b - D x
     {
-        ProfScope ps(&ctx->prof, "dw_f64_residual", ptr_bytes_dw(op, op, P64, V) + fb);
+        ProfScope ps(&ctx->prof, "dw_f64_residual", ptr_bytes_dw(op, op, op, V) + fb);
         FieldRef in{xb + (long long)r * fb, 0, 0, 0}, out{rb + (long long)r * fb, 0, 0, 0},
             sub{bb + (long long)r * fb, 0, 0, 0};
-        if ((rc = launch_dw(op, op, P64, g, ctx->m0, in, out, U64, nullptr, 1, &sub, st))) return rc;
+        if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, 1, &sub, st))) return rc;
     }
     explicit_res++;
     {
@@ -556,7 +557,7 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
         }
         if ((rc = launch_to_internal(op, x_dev, xb, V, nrhs, st))) return rc;
         FieldRef in{xb, fb, 0, 0}, out{rb, fb, 0, 0}, sub{bb, fb, 0, 0};
-        if ((rc = launch_dw(op, op, P64, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st))) return rc;
+        if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st))) return rc;
         explicit_res++;
     } else {
         DW_CUDA_TRY(cudaMemsetAsync(xb, 0, (size_t)nrhs * fb, st));
