@@ -205,8 +205,13 @@ int dw_apply_f32_noalloc(const int* dims, double m0, const double* U, const doub
  * queued requests are taken first-in first-out, and a later request that fits
  * may start while an earlier one waits for memory. Each admitted request runs
  * fgmresdr_solve on its own CUDA stream and context, so concurrent requests
- * overlap on the device. Not part of the paper: this is the request loop the
- * solver is deployed behind. */
+ * overlap on the device. A finished request's context (converted gauge field,
+ * Krylov workspace) stays on the device, counted in the budget, and is taken
+ * over by a later request that passes the same host gauge pointer and lattice
+ * (so that buffer must not change while the server lives); idle contexts are
+ * freed least recently used first when admission needs the memory.
+ * Not part of the paper: this is the request loop the solver is deployed
+ * behind. */
 typedef struct {
     dw_lattice lattice;      /* dims, domain block, m0                                     */
     const double* U;         /* host, canonical gauge field; valid until the request is done */
@@ -219,6 +224,7 @@ typedef struct {
     size_t budget_bytes, in_use_bytes, peak_bytes;
     int running, queued;
     long long completed;
+    long long reused; /* requests that took over a cached context */
 } dw_server_status;
 
 typedef struct dw_server dw_server;
@@ -240,7 +246,8 @@ int dw_server_wait(dw_server* s, uint64_t id, double timeout_s, int* status, dw_
 /* Cancels a queued request; running requests are not interrupted. */
 int dw_server_cancel(dw_server* s, uint64_t id);
 int dw_server_info(dw_server* s, dw_server_status* out);
-/* Cancels queued requests, waits for running ones, frees everything. */
+/* in_use_bytes includes idle cached contexts.
+ * dw_server_destroy cancels queued requests, waits for running ones, frees everything. */
 void dw_server_destroy(dw_server* s);
 
 #ifdef __cplusplus

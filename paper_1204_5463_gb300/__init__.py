@@ -53,7 +53,8 @@ class dw_request(ctypes.Structure):
 
 class dw_server_status(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
-                ("running", ctypes.c_int), ("queued", ctypes.c_int), ("completed", ctypes.c_longlong)]
+                ("running", ctypes.c_int), ("queued", ctypes.c_int), ("completed", ctypes.c_longlong),
+                ("reused", ctypes.c_longlong)]
 
 
 class dw_kernel_stat(ctypes.Structure):

@@ -35,6 +35,20 @@ struct link_word<P32> {
     typedef float2 type;
 };
 
+// asynchronous global -> shared copy of one 4/8/16-byte word
+template <class W>
+__device__ __forceinline__ void cp_async_word(W* smem_dst, const W* gsrc) {
+    static_assert(sizeof(W) == 4 || sizeof(W) == 8 || sizeof(W) == 16, "cp.async word size");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(W) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(sizeof(W)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <class C>
 __device__ __forceinline__ void block_sum3(C& a, C& b, C& c, C* red) {
 #pragma unroll
@@ -107,27 +121,41 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     for (int j = 0; j < 4; ++j) xg[j] = D[j] * g.b[j] + lx[j];
     const long long s = site_index(g, xg);
 
-    // 1. own links -> shared memory (raw storage words); in the general mode
-    //    also the domain's own iterate x (read by interior hops of the residual)
+    // 1. asynchronous copies global -> shared, all in flight together: the
+    //    domain's own links (raw storage words) and, in the general mode, its
+    //    own iterate x in storage layout (stride T), read by interior hops
     const char* lsh = reinterpret_cast<const char*>(link_sh);
+    char* xsh = reinterpret_cast<char*>(rho_sh);  // reused for rho in the MR phase
     if (act) {
         const LW* Ug = reinterpret_cast<const LW*>(U);
 #pragma unroll 4
-        for (int c = 0; c < 36; ++c) link_sh[c * T + tid] = Ug[(long long)c * g.V + s];
+        for (int c = 0; c < 36; ++c) cp_async_word(&link_sh[c * T + tid], &Ug[(long long)c * g.V + s]);
         if (mode == 2) {
-            cx<C> xo[12];
-            load_spinor<PS, C>(xb, g.V, s, xo);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) rho_sh[c * T + tid] = xo[c];
+            if constexpr (PS == P64) {
+                for (int c = 0; c < 12; ++c)
+                    cp_async_word(reinterpret_cast<double2*>(xsh) + c * T + tid,
+                                  reinterpret_cast<const double2*>(xb) + c * g.V + s);
+            } else if constexpr (PS == P32) {
+                for (int q = 0; q < 6; ++q)
+                    cp_async_word(reinterpret_cast<float4*>(xsh) + q * T + tid,
+                                  reinterpret_cast<const float4*>(xb) + q * g.V + s);
+            } else {
+                for (int q = 0; q < 3; ++q)
+                    cp_async_word(reinterpret_cast<uint4*>(xsh) + q * T + tid,
+                                  reinterpret_cast<const uint4*>(xb) + q * g.V + s);
+                cp_async_word(reinterpret_cast<float*>(reinterpret_cast<uint4*>(xsh) + 3 * T) + tid,
+                              reinterpret_cast<const float*>(reinterpret_cast<const uint4*>(xb) + 3 * g.V) + s);
+            }
         }
     }
+    cx<C> rho[12], y[12];
+    if (act) load_spinor<PS, C>(vb, g.V, s, rho);  // overlaps the copies above
+    cp_async_wait();
     __syncthreads();
 
     // 2. residual r = v - D x at this site: interior neighbours and every
     //    forward link from shared memory, boundary neighbours through L2
-    cx<C> rho[12], y[12];
     if (act) {
-        load_spinor<PS, C>(vb, g.V, s, rho);
         if (mode != 0) {
             cx<C> acc[12], psi[12], u[9];
 #pragma unroll
@@ -137,8 +165,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     {                                                                                        \
         if (lx[MU] + 1 < g.b[MU]) {                                                          \
             if (general) {                                                                   \
-                const int tn = tid + lstride[MU];                                            \
-                _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];  \
+                load_spinor<PS, C, false>(xsh, T, tid + lstride[MU], psi);                   \
                 load_link<PL, C, false>(lsh, T, MU, tid, u);                                 \
                 hop<MU, +1, C>(psi, u, acc);                                                 \
             }                                                                                \
@@ -150,7 +177,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
         if (lx[MU] >= 1) {                                                                   \
             if (general) {                                                                   \
                 const int tn = tid - lstride[MU];                                            \
-                _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];  \
+                load_spinor<PS, C, false>(xsh, T, tn, psi);                                  \
                 load_link<PL, C, false>(lsh, T, MU, tn, u);                                  \
                 hop<MU, -1, C>(psi, u, acc);                                                 \
             }                                                                                \
@@ -168,8 +195,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
 #undef SAP_RES_HOPS
             const C half = (C)0.5;
             if (general) {
+                load_spinor<PS, C, false>(xsh, T, tid, psi);
 #pragma unroll
-                for (int c = 0; c < 12; ++c) rho[c] = rho[c] - (diag * rho_sh[c * T + tid] - half * acc[c]);
+                for (int c = 0; c < 12; ++c) rho[c] = rho[c] - (diag * psi[c] - half * acc[c]);
             } else {
 #pragma unroll
                 for (int c = 0; c < 12; ++c) rho[c] = rho[c] + half * acc[c];

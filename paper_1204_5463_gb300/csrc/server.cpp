@@ -10,6 +10,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -23,6 +24,8 @@ using clk = std::chrono::steady_clock;
 struct Req {
     dw_request r;
     size_t bytes = 0;
+    dw_ctx* ctx = nullptr;  // cached context handed to this request, if any
+    cudaStream_t st = nullptr;
     int state = 0;  // 0 queued, 1 running, 2 done
     int status = DW_OK;
     bool cancelled = false;
@@ -32,8 +35,20 @@ struct Req {
 
 }  // namespace
 
+// An idle context kept after its request finished: the converted gauge field
+// and the Krylov workspace stay on the device for the next request that names
+// the same host gauge buffer and lattice.
+struct CachedCtx {
+    const double* U;
+    int dims[4], block[4];
+    dw_ctx* ctx;
+    cudaStream_t st;
+    size_t bytes;
+};
+
 struct dw_server {
     size_t budget = 0;
+    std::list<CachedCtx> cache;  // most recently used first; counted in in_use
     int max_slots = 1;
     int device = 0;
     std::mutex mu;
@@ -42,7 +57,7 @@ struct dw_server {
     std::map<uint64_t, Req> reqs;
     size_t in_use = 0, peak = 0;
     int running = 0;
-    long long completed = 0;
+    long long completed = 0, reused = 0;
     uint64_t next_id = 1;
     bool stop = false;
     std::vector<std::thread> workers;
@@ -64,6 +79,18 @@ size_t request_bytes(const dw_request* q) {
     return (size_t)(gauge + (long long)P.nrhs * per_rhs + (long long)(P.k > 0 ? P.k : 1) * sb + (8LL << 20));
 }
 
+bool same_field(const CachedCtx& c, const dw_request& r) {
+    if (c.U != r.U) return false;
+    for (int j = 0; j < 4; ++j)
+        if (c.dims[j] != r.lattice.dims[j] || c.block[j] != r.lattice.block[j]) return false;
+    return true;
+}
+
+void destroy_cached(CachedCtx& c) {
+    dw_destroy(c.ctx);
+    cudaStreamDestroy(c.st);
+}
+
 void run_request(dw_server* s, uint64_t id) {
     Req* rq;
     {
@@ -71,28 +98,46 @@ void run_request(dw_server* s, uint64_t id) {
         rq = &s->reqs[id];
     }
     int rc = DW_OK;
-    cudaStream_t st = nullptr;
-    dw_ctx* ctx = nullptr;
+    cudaStream_t st = rq->st;
+    dw_ctx* ctx = rq->ctx;
     dw_stats S{};
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        rc = DW_ECUDA;
+    if (!ctx) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            st = nullptr;
+            rc = DW_ECUDA;
+        }
+        if (rc == DW_OK) rc = dw_create(&rq->r.lattice, st, &ctx);
+        if (rc == DW_OK) rc = dw_set_gauge(ctx, rq->r.U, 0);
+    } else {
+        rc = dw_set_mass(ctx, rq->r.lattice.m0);
     }
-    if (rc == DW_OK) rc = dw_create(&rq->r.lattice, st, &ctx);
-    if (rc == DW_OK) rc = dw_set_gauge(ctx, rq->r.U, 0);
     if (rc == DW_OK) {
         dw_solver_params P = rq->r.params;
         P.host_buffers = 1;
         rc = fgmresdr_solve(ctx, rq->r.b, rq->r.x, &P, &S);
     }
-    if (ctx) dw_destroy(ctx);
-    if (st) cudaStreamDestroy(st);
+    const bool keep = ctx && (rc == DW_OK || rc == DW_ENOTCONV);
+    if (!keep) {
+        if (ctx) dw_destroy(ctx);
+        if (st) cudaStreamDestroy(st);
+    }
     std::lock_guard<std::mutex> lock(s->mu);
     rq->status = rc;
     rq->stats = S;
     rq->state = 2;
     rq->t_done = clk::now();
-    s->in_use -= rq->bytes;
+    if (keep) {
+        CachedCtx c;
+        c.U = rq->r.U;
+        for (int j = 0; j < 4; ++j) c.dims[j] = rq->r.lattice.dims[j], c.block[j] = rq->r.lattice.block[j];
+        c.ctx = ctx;
+        c.st = st;
+        c.bytes = rq->bytes;  // stays counted in in_use while cached
+        s->cache.push_front(c);
+    } else {
+        s->in_use -= rq->bytes;
+    }
     s->running--;
     s->completed++;
     s->cv_done.notify_all();
@@ -100,10 +145,41 @@ void run_request(dw_server* s, uint64_t id) {
 }
 
 // First queued request that fits (FIFO order, later requests may backfill).
+// A request on a cached gauge field takes over that context (its bytes are
+// already counted); otherwise idle cached contexts are evicted, least
+// recently used first, while that makes room.
 bool pick(dw_server* s, uint64_t* id) {
     for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
         Req& r = s->reqs[*it];
-        if (s->in_use + r.bytes <= s->budget) {
+        for (auto c = s->cache.begin(); c != s->cache.end(); ++c)
+            if (same_field(*c, r.r)) {
+                const size_t need = r.bytes > c->bytes ? r.bytes - c->bytes : 0;
+                size_t idle = 0;
+                for (auto& o : s->cache)
+                    if (&o != &*c) idle += o.bytes;
+                if (s->in_use + need > s->budget + idle) break;
+                r.ctx = c->ctx;
+                r.st = c->st;
+                s->reused++;
+                s->in_use -= c->bytes;
+                s->cache.erase(c);
+                while (s->in_use + r.bytes > s->budget && !s->cache.empty()) {
+                    s->in_use -= s->cache.back().bytes;
+                    destroy_cached(s->cache.back());
+                    s->cache.pop_back();
+                }
+                *id = *it;
+                s->queue.erase(it);
+                return true;
+            }
+        size_t idle = 0;
+        for (auto& o : s->cache) idle += o.bytes;
+        if (s->in_use + r.bytes <= s->budget + idle) {
+            while (s->in_use + r.bytes > s->budget && !s->cache.empty()) {
+                s->in_use -= s->cache.back().bytes;
+                destroy_cached(s->cache.back());
+                s->cache.pop_back();
+            }
             *id = *it;
             s->queue.erase(it);
             return true;
@@ -228,6 +304,7 @@ int dw_server_info(dw_server* s, dw_server_status* out) {
     out->running = s->running;
     out->queued = (int)s->queue.size();
     out->completed = s->completed;
+    out->reused = s->reused;
     return DW_OK;
 }
 
@@ -246,6 +323,7 @@ void dw_server_destroy(dw_server* s) {
     }
     s->cv_work.notify_all();
     for (auto& t : s->workers) t.join();
+    for (auto& c : s->cache) destroy_cached(c);
     delete s;
 }
 

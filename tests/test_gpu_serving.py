@@ -62,7 +62,8 @@ def test_server_results_equal_alone_and_in_mix(dw):
             status, S, lat = dw.dw_server_wait(srv, rid, 300)
             assert status == dw.DW_OK and lat > 0
         info = dw.dw_server_info(srv)
-        assert info["completed"] == len(reqs) and info["in_use_bytes"] == 0
+        assert info["completed"] == len(reqs) and info["running"] == 0
+        assert info["in_use_bytes"] <= info["budget_bytes"]  # idle cached contexts only
     finally:
         dw.dw_server_destroy(srv)
     for q, x in zip(reqs, xs):
@@ -125,5 +126,26 @@ def test_server_rejects_and_cancels(dw):
         for rid in ids[:-1]:
             status, _, _ = dw.dw_server_wait(srv, rid, 300)
             assert status == dw.DW_OK
+    finally:
+        dw.dw_server_destroy(srv)
+
+
+def test_server_reuses_resident_gauge_field(dw):
+    """A second request on the same gauge buffer takes over the cached context
+    (gauge copy and workspace stay on the device) and gives the same answer."""
+    q = _requests()[1]
+    srv = dw.dw_server_create(8 << 30, 1)
+    try:
+        xs, keep = [], []
+        for _ in range(2):
+            x = np.zeros_like(q["b"])
+            r = dw.make_request(q["dims"], q["block"], q["m0"], q["U"], q["b"], x, _params(dw, q["nrhs"]))
+            keep.append(r)
+            xs.append(x)
+            rid = dw.dw_server_submit(srv, r)
+            status, _, _ = dw.dw_server_wait(srv, rid, 300)
+            assert status == dw.DW_OK
+        assert dw.dw_server_info(srv)["reused"] == 1
+        assert np.array_equal(xs[0], xs[1])
     finally:
         dw.dw_server_destroy(srv)
