@@ -253,6 +253,75 @@ def run_serving(args, rank, world):
     return 0
 
 
+def run_workload(args, rank, world):
+    """The batched (24^3x48, 12 point sources) and mixed-precision (32^3x64,
+    FP16/BF16 SAP, FGMRES-DR(40,16) vs restarted FGMRES(40)) workloads."""
+    import numpy as np
+    import torch
+
+    import fieldgen as fg
+    import paper_1204_5463_gb300 as dw
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = dict(fg.lattice_configs()[args.workload])
+    dims = cfg["dims"]
+    stream = torch.cuda.current_stream()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).reshape(-1).copy()).cuda()
+
+    U = fg.gauge_field(dims, cfg["eps"], cfg["seed"])
+    Ud = dev(U)
+    out = {"workload": args.workload, "lattice": list(dims), "m0": cfg["m0"], "eps": cfg["eps"],
+           "target_min_abs_eig": cfg["target_min_abs_eig"], "runs": []}
+
+    def solve(block, b, nrhs, **kw):
+        ctx = dw.dw_create(dims, block, cfg["m0"], stream.cuda_stream)
+        try:
+            dw.dw_set_gauge(ctx, Ud, True)
+            P = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                                     mr_steps=cfg["mr_steps"], nrhs=nrhs, **kw)
+            bd = dev(b)
+            xd = torch.zeros_like(bd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S = dw.fgmresdr_solve(ctx, bd, xd, P, allow_notconv=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            return S, dt
+        finally:
+            dw.dw_destroy(ctx)
+
+    if args.workload.startswith("batched"):
+        b = fg.point_sources(dims)
+        blocks = [tuple(cfg["block"])]
+        if not args.no_tune:
+            bt, table = dw.dw_autotune_block(dims, cfg["m0"], Ud, dev(b[:2]),
+                                             dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=1e-6, sap_cycles=5,
+                                                                  mr_steps=4, nrhs=2, sap_prec=dw.DW_F16))
+            out["autotune"] = {"best": bt, "candidates": [
+                {"block": t[0], "seconds": t[1], "iterations": t[2], "status": t[3]} for t in table]}
+            if bt not in blocks:
+                blocks.append(bt)
+        for blk in blocks:
+            S, dt = solve(blk, b, 12, sap_prec=dw.DW_F16)
+            out["runs"].append({"block": list(blk), "nrhs": 12, "sap_prec": "f16", "seconds": dt,
+                                "solves_per_s": S.converged / dt, "converged": S.converged,
+                                "iterations_max": S.iterations, "cycles": S.cycles,
+                                "true_rel_res_max": max(S.true_rel_res[i] for i in range(12))})
+    else:
+        b = fg.gaussian_source(dims, 1)
+        for prec, pname in ((dw.DW_F16, "f16"), (dw.DW_BF16, "bf16")):
+            for k, cyc in ((cfg["k"], 400), (0, args.k0_cycles)):
+                S, dt = solve(cfg["block"], b, 1, sap_prec=prec, k=k, max_cycles=cyc)
+                out["runs"].append({"sap_prec": pname, "m": cfg["m"], "k": k, "seconds": dt,
+                                    "converged": S.converged, "iterations": S.iterations, "cycles": S.cycles,
+                                    "clean_restarts": S.clean_restarts, "true_rel_res": S.true_rel_res[0]})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,6 +338,10 @@ def main():
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="wilson_16x16x16x32 (default, the benchmark line), batched_24x24x24x48, mixed_32x32x32x64")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--k0-cycles", type=int, default=40, help="cycle cap of the restarted FGMRES comparison")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -286,6 +359,8 @@ def main():
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.serving:
         return run_serving(args, rank, world)
+    if args.workload != WORKLOAD:
+        return run_workload(args, rank, world)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)
         if dist:

@@ -175,6 +175,32 @@ long long dw_kernel_launches(void);
 /* Copies up to max entries into out, sets *n; reset != 0 clears the totals. */
 int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset);
 
+/* ---- domain-tile autotuner ------------------------------------------------
+ * Chooses the SAP domain block for a lattice by the time to solution of a
+ * calibration solve per candidate (the block changes the preconditioner, so
+ * iteration counts change with it). Candidates: block[j] divides dims[j] with
+ * dims[j] / block[j] even (red-black colouring, Sec. 2), 32..1024 sites per
+ * domain, aspect ratio <= 2, SAP shared memory within one CTA; the twelve
+ * closest to 256 sites per domain (most isotropic first) are timed.
+ * L: dims and m0 (block ignored); U: device canonical FP64 gauge field;
+ * b: device canonical right-hand sides (P->nrhs fields); P: the calibration
+ * solve (a looser tol keeps it short; host_buffers and use_x0 are ignored).
+ * Writes the fastest converged block to best_block; when results is non-NULL
+ * also up to max_results timed candidates and their count to *n_results.
+ * The choice is cached per (dims, nrhs, precisions, m, k, SAP cycles, MR
+ * steps): a later call without results returns the cached block at once.
+ * Allocates one output field on the stream; DW_ENOTCONV if no candidate
+ * converged. */
+typedef struct {
+    int block[4];
+    double seconds;  /* wall time of the calibration solve (1e300 if it failed) */
+    int iterations;
+    int status;
+} dw_tune_entry;
+
+int dw_autotune_block(const dw_lattice* L, const double* U, const double* b, const dw_solver_params* P,
+                      void* cuda_stream, int* best_block, dw_tune_entry* results, int max_results, int* n_results);
+
 /* ---- allocation-free operator ----------------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that
  * cannot call cudaMalloc (code inside a pre-reserved memory pool, allocators

@@ -46,6 +46,11 @@ class dw_stats(ctypes.Structure):
                 ("time_s", ctypes.c_double)]
 
 
+class dw_tune_entry(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int * 4), ("seconds", ctypes.c_double), ("iterations", ctypes.c_int),
+                ("status", ctypes.c_int)]
+
+
 class dw_request(ctypes.Structure):
     _fields_ = [("lattice", dw_lattice), ("U", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("params", dw_solver_params)]
@@ -77,6 +82,8 @@ _SIGS = {
     "dw_profile": ([_P, _I], _I),
     "dw_kernel_launches": ([], ctypes.c_longlong),
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
+    "dw_autotune_block": ([ctypes.POINTER(dw_lattice), _P, _P, ctypes.POINTER(dw_solver_params), _P,
+                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dw_tune_entry), _I, ctypes.POINTER(_I)], _I),
     "dw_apply_f32_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_double, _P, _P, _P, _P], _I),
     "dw_request_bytes": ([ctypes.POINTER(dw_request)], ctypes.c_size_t),
     "dw_server_create": ([ctypes.c_size_t, _I, ctypes.POINTER(_P)], _I),
@@ -192,6 +199,20 @@ def dw_profile_read(ctx, reset: bool = False) -> dict:
     _check(_lib.dw_profile_read(ctx, buf, 64, ctypes.byref(n), int(bool(reset))), "dw_profile_read")
     return {buf[i].name.decode(): dict(launches=buf[i].launches, total_ms=buf[i].total_ms, bytes=buf[i].bytes)
             for i in range(min(n.value, 64))}
+
+
+def dw_autotune_block(dims, m0: float, U, b, params: dw_solver_params, stream=None, with_results: bool = True):
+    """Best SAP domain block by calibration-solve time; returns (block, [(block, seconds, iterations, status)])."""
+    L = dw_lattice((ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(0, 0, 0, 0), float(m0))
+    best = (ctypes.c_int * 4)()
+    res = (dw_tune_entry * 256)() if with_results else None
+    n = _I(0)
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(_lib.dw_autotune_block(ctypes.byref(L), _ptr(U), _ptr(b), ctypes.byref(params), s, best,
+                                  res, 256 if with_results else 0, ctypes.byref(n)), "dw_autotune_block")
+    table = [(tuple(res[i].block), res[i].seconds, res[i].iterations, res[i].status)
+             for i in range(min(n.value, 256))] if with_results else []
+    return tuple(best), table
 
 
 def dw_apply_f32_noalloc(dims, m0: float, U, inp, out, stream=None) -> None:
