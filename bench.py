@@ -123,6 +123,51 @@ def kernel_traffic(name):
     return e["bytes_per_launch"] * e.get("scale", 1.0)
 
 
+def dw_bandwidth(peaks, reps=10):
+    """The full-lattice stencil alone on a 24^3 x 48 lattice (its links and
+    fields, 318 MB in FP32, exceed L2): algorithmic bytes per site (links +
+    input + output: 960 B FP64, 480 B FP32, 248 B FP16 with scales) over the
+    kernel's CUDA-event time, per storage precision. L2 is flushed (a 256 MB
+    write) before every call; each call converts its input to the internal
+    layout right before the stencil, so part of that input can still be in L2."""
+    import numpy as np
+    import torch
+
+    import fieldgen as fg
+    import paper_1204_5463_gb300 as dw
+
+    dims = (24, 24, 24, 48)
+    U = fg.gauge_field(dims, 0.5, 0)
+    psi = fg.gaussian_source(dims, 7)
+    stream = torch.cuda.current_stream()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).reshape(-1).copy()).cuda()
+
+    ctx = dw.dw_create(dims, (4, 4, 4, 4), -0.5, stream.cuda_stream)
+    dw.dw_set_gauge(ctx, dev(U), True)
+    ind = dev(psi)
+    outd = torch.empty_like(ind)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"lattice": list(dims), "l2": "256 MB write before each call", "reps": reps}
+    for name, prec in (("f64", dw.DW_F64), ("f32", dw.DW_F32), ("f16", dw.DW_F16)):
+        dw.dw_apply(ctx, ind, outd, prec)  # builds this precision's link copy
+        dw.dw_profile(ctx, True)
+        dw.dw_profile_read(ctx, reset=True)
+        for _ in range(reps):
+            flush.zero_()
+            dw.dw_apply(ctx, ind, outd, prec)
+        torch.cuda.synchronize()
+        d = dw.dw_profile_read(ctx, reset=True)["dw_" + name]
+        dw.dw_profile(ctx, False)
+        avg_s = d["total_ms"] / d["launches"] / 1e3
+        gbs = d["bytes"] / d["launches"] / avg_s / 1e9
+        out[name] = {"GB/s": gbs, "frac": gbs / peaks["hbm_gbs"], "avg_us": avg_s * 1e6,
+                     "bytes_per_site": d["bytes"] / d["launches"] / fg.volume(dims)}
+    dw.dw_destroy(ctx)
+    return out
+
+
 def oracle_sample(cfg, U, b, n_iter):
     """Seconds per Arnoldi step of the oracle on this workload (bounded sample)."""
     import oracle
@@ -334,6 +379,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sap-prec", default="f32")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-dw-bw", action="store_true", help="skip the stand-alone D_w bandwidth measurement")
     ap.add_argument("--serving", action="store_true", help="run the serving measurement instead")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
@@ -495,6 +541,7 @@ def main():
     tr = kernel_traffic(dom)
     roof.update({"kernel": dom, "traffic": tr, "launches": d["launches"], "avg_us": 1e3 * avg_ms})
     shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4) for k, v in prof.items()}
+    dwbw = None if args.no_dw_bw else dw_bandwidth(peaks)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -513,6 +560,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "mixed_batched": mb,
+        "dw_apply": dwbw,
     }
     if rank == 0 and not args.no_cpu_baseline:
         t_it, n = oracle_sample(cfg, U, b, 3)

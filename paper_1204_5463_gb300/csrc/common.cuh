@@ -402,9 +402,9 @@ __device__ __forceinline__ void su3_mul(const cx<C> u[9], const cx<C> h[3], cx<C
     }
 }
 
+// upper two spin rows of (1 + SIGN gamma_MU) psi
 template <int MU, int SIGN, class C>
-__device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C> acc[12]) {
-    cx<C> h0[3], h1[3], k0[3], k1[3];
+__device__ __forceinline__ void project(const cx<C> psi[12], cx<C> h0[3], cx<C> h1[3]) {
     const C s = (C)SIGN;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -423,8 +423,12 @@ __device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C>
             h1[c] = p1 + s * p3;
         }
     }
-    su3_mul<C, (SIGN < 0)>(u, h0, k0);
-    su3_mul<C, (SIGN < 0)>(u, h1, k1);
+}
+
+// acc += the four spin rows rebuilt from the multiplied upper rows k0, k1
+template <int MU, int SIGN, class C>
+__device__ __forceinline__ void reconstruct(const cx<C> k0[3], const cx<C> k1[3], cx<C> acc[12]) {
+    const C s = (C)SIGN;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         acc[c] = acc[c] + k0[c];
@@ -443,6 +447,15 @@ __device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C>
             acc[9 + c] = acc[9 + c] + s * k1[c];
         }
     }
+}
+
+template <int MU, int SIGN, class C>
+__device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C> acc[12]) {
+    cx<C> h0[3], h1[3], k0[3], k1[3];
+    project<MU, SIGN, C>(psi, h0, h1);
+    su3_mul<C, (SIGN < 0)>(u, h0, k0);
+    su3_mul<C, (SIGN < 0)>(u, h1, k1);
+    reconstruct<MU, SIGN, C>(k0, k1, acc);
 }
 
 // ---------------------------------------------------------------------------

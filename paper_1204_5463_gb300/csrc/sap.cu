@@ -22,19 +22,6 @@ namespace dwk {
 
 namespace {
 
-template <int PL>
-struct link_word {
-    typedef uint32_t type;
-};
-template <>
-struct link_word<P64> {
-    typedef double2 type;
-};
-template <>
-struct link_word<P32> {
-    typedef float2 type;
-};
-
 // asynchronous global -> shared copy of one 4/8/16-byte word
 template <class W>
 __device__ __forceinline__ void cp_async_word(W* smem_dst, const W* gsrc) {
@@ -47,6 +34,129 @@ __device__ __forceinline__ void cp_async_word(W* smem_dst, const W* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// The domain's own links in shared memory, packed so that one link matrix
+// (9 complex entries) is read with as few wide loads as possible:
+//   P64      double2 [4][9][T]                                          (9 x 16 B loads)
+//   P32      float2 [4][9][T]                                           (9 x 8 B loads)
+//   P16/B16  uint4 [4][2][T] (entry quads) + uint32 [4][T] (entry 8)    (2 x 16 B + 4 B)
+// Staging copies each global storage word (component-major [4][9][V]) into
+// its slot with cp.async, so the repacking costs nothing at run time. (FP32
+// entry pairs packed as float4 measured no faster than plain float2 loads.)
+template <int PL>
+struct LinkSh;
+template <>
+struct LinkSh<P64> {
+    static constexpr int kBytes = 576;
+    static __device__ __forceinline__ void stage(unsigned char* L, int T, int t, const char* U, long long V,
+                                                 long long s) {
+        const double2* Ug = reinterpret_cast<const double2*>(U);
+        double2* A = reinterpret_cast<double2*>(L);
+#pragma unroll 4
+        for (int c = 0; c < 36; ++c) cp_async_word(&A[c * T + t], &Ug[(long long)c * V + s]);
+    }
+    template <class C>
+    static __device__ __forceinline__ void load(const unsigned char* L, int T, int mu, int t, cx<C> u[9]) {
+        const double2* A = reinterpret_cast<const double2*>(L) + mu * 9 * T;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const double2 v = A[c * T + t];
+            u[c] = mk<C>((C)v.x, (C)v.y);
+        }
+    }
+};
+template <>
+struct LinkSh<P32> {
+    static constexpr int kBytes = 288;
+    static __device__ __forceinline__ void stage(unsigned char* L, int T, int t, const char* U, long long V,
+                                                 long long s) {
+        const float2* Ug = reinterpret_cast<const float2*>(U);
+        float2* A = reinterpret_cast<float2*>(L);
+#pragma unroll 4
+        for (int c = 0; c < 36; ++c) cp_async_word(&A[c * T + t], &Ug[(long long)c * V + s]);
+    }
+    template <class C>
+    static __device__ __forceinline__ void load(const unsigned char* L, int T, int mu, int t, cx<C> u[9]) {
+        const float2* A = reinterpret_cast<const float2*>(L) + mu * 9 * T;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const float2 v = A[c * T + t];
+            u[c] = mk<C>((C)v.x, (C)v.y);
+        }
+    }
+};
+template <int PL>
+struct LinkSh16 {
+    static constexpr int kBytes = 144;
+    static __device__ __forceinline__ void stage(unsigned char* L, int T, int t, const char* U, long long V,
+                                                 long long s) {
+        const uint32_t* Ug = reinterpret_cast<const uint32_t*>(U);
+        uint32_t* A = reinterpret_cast<uint32_t*>(L);            // uint4 [4][2][T] seen as words
+        uint32_t* B = reinterpret_cast<uint32_t*>(L + 128 * T);  // uint32 [4][T]
+#pragma unroll 2
+        for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                cp_async_word(&A[4 * ((mu * 2 + (c >> 2)) * T + t) + (c & 3)], &Ug[(long long)(mu * 9 + c) * V + s]);
+            cp_async_word(&B[mu * T + t], &Ug[(long long)(mu * 9 + 8) * V + s]);
+        }
+    }
+    template <class C>
+    static __device__ __forceinline__ void load(const unsigned char* L, int T, int mu, int t, cx<C> u[9]) {
+        constexpr int bf = (PL == PB16);
+        const uint4* A = reinterpret_cast<const uint4*>(L) + mu * 2 * T;
+        const uint32_t* B = reinterpret_cast<const uint32_t*>(L + 128 * T);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint4 v = A[q * T + t];
+            const float2 a = h2_to_f2(v.x, bf), b = h2_to_f2(v.y, bf), c = h2_to_f2(v.z, bf), d = h2_to_f2(v.w, bf);
+            u[4 * q] = mk<C>((C)a.x, (C)a.y);
+            u[4 * q + 1] = mk<C>((C)b.x, (C)b.y);
+            u[4 * q + 2] = mk<C>((C)c.x, (C)c.y);
+            u[4 * q + 3] = mk<C>((C)d.x, (C)d.y);
+        }
+        const float2 w = h2_to_f2(B[mu * T + t], bf);
+        u[8] = mk<C>((C)w.x, (C)w.y);
+    }
+};
+template <>
+struct LinkSh<P16> : LinkSh16<P16> {};
+template <>
+struct LinkSh<PB16> : LinkSh16<PB16> {};
+
+// The MR iterate rho in shared memory: FP32 as float4 [6][T] (two complex per
+// load), FP64 as double2 [12][T].
+template <class C>
+__device__ __forceinline__ void rho_store(unsigned char* R, int T, int t, const cx<C> v[12]) {
+    if constexpr (sizeof(C) == 4) {
+        float4* p = reinterpret_cast<float4*>(R);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) p[q * T + t] = make_float4(v[2 * q].re, v[2 * q].im, v[2 * q + 1].re, v[2 * q + 1].im);
+    } else {
+        double2* p = reinterpret_cast<double2*>(R);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[c * T + t] = make_double2(v[c].re, v[c].im);
+    }
+}
+template <class C>
+__device__ __forceinline__ void rho_load(const unsigned char* R, int T, int t, cx<C> v[12]) {
+    if constexpr (sizeof(C) == 4) {
+        const float4* p = reinterpret_cast<const float4*>(R);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float4 a = p[q * T + t];
+            v[2 * q] = mk<C>(a.x, a.y);
+            v[2 * q + 1] = mk<C>(a.z, a.w);
+        }
+    } else {
+        const double2* p = reinterpret_cast<const double2*>(R);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const double2 a = p[c * T + t];
+            v[c] = mk<C>(a.x, a.y);
+        }
+    }
 }
 
 template <class C>
@@ -77,15 +187,15 @@ __device__ __forceinline__ void block_sum3(C& a, C& b, C& c, C* red) {
 }
 
 template <int PS, int PL, class C, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1) sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref,
-                                                         const char* __restrict__ U, const int* jtab, int nrhs,
-                                                         int colour, int nmr, int mode) {
-    typedef typename link_word<PL>::type LW;
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
+    sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref, const char* __restrict__ U, const int* jtab,
+                     int nrhs, int colour, int nmr, int mode) {
+    typedef LinkSh<PL> LS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x;
-    cx<C>* rho_sh = reinterpret_cast<cx<C>*>(smem);                           // [12][T] complex
-    LW* link_sh = reinterpret_cast<LW*>(smem + sizeof(C) * 24 * T);          // [4][9][T]
-    C* red = reinterpret_cast<C*>(smem + sizeof(C) * 24 * T + sizeof(LW) * 36 * T);  // [32][3]
+    unsigned char* rsh = smem;                                   // rho (MR phase) / own x (residual phase)
+    unsigned char* lsh = smem + sizeof(C) * 24 * T;              // links
+    C* red = reinterpret_cast<C*>(lsh + (size_t)LS::kBytes * T);  // [32][3]
 
     const int r = blockIdx.x % nrhs;
     const int e = blockIdx.x / nrhs;
@@ -116,34 +226,30 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
         lx[2] = q % g.b[2];
         lx[3] = q / g.b[2];
     }
-    const int lstride[4] = {1, g.b[0], g.b[0] * g.b[1], g.b[0] * g.b[1] * g.b[2]};
 #pragma unroll
     for (int j = 0; j < 4; ++j) xg[j] = D[j] * g.b[j] + lx[j];
     const long long s = site_index(g, xg);
+    const int ls1 = g.b[0], ls2 = g.b[0] * g.b[1], ls3 = g.b[0] * g.b[1] * g.b[2];  // in-domain strides
 
     // 1. asynchronous copies global -> shared, all in flight together: the
-    //    domain's own links (raw storage words) and, in the general mode, its
-    //    own iterate x in storage layout (stride T), read by interior hops
-    const char* lsh = reinterpret_cast<const char*>(link_sh);
-    char* xsh = reinterpret_cast<char*>(rho_sh);  // reused for rho in the MR phase
+    //    domain's own links and, in the general mode, its own iterate x in
+    //    storage layout (stride T), read by interior hops
     if (act) {
-        const LW* Ug = reinterpret_cast<const LW*>(U);
-#pragma unroll 4
-        for (int c = 0; c < 36; ++c) cp_async_word(&link_sh[c * T + tid], &Ug[(long long)c * g.V + s]);
+        LS::stage(lsh, T, tid, U, g.V, s);
         if (mode == 2) {
             if constexpr (PS == P64) {
                 for (int c = 0; c < 12; ++c)
-                    cp_async_word(reinterpret_cast<double2*>(xsh) + c * T + tid,
+                    cp_async_word(reinterpret_cast<double2*>(rsh) + c * T + tid,
                                   reinterpret_cast<const double2*>(xb) + c * g.V + s);
             } else if constexpr (PS == P32) {
                 for (int q = 0; q < 6; ++q)
-                    cp_async_word(reinterpret_cast<float4*>(xsh) + q * T + tid,
+                    cp_async_word(reinterpret_cast<float4*>(rsh) + q * T + tid,
                                   reinterpret_cast<const float4*>(xb) + q * g.V + s);
             } else {
                 for (int q = 0; q < 3; ++q)
-                    cp_async_word(reinterpret_cast<uint4*>(xsh) + q * T + tid,
+                    cp_async_word(reinterpret_cast<uint4*>(rsh) + q * T + tid,
                                   reinterpret_cast<const uint4*>(xb) + q * g.V + s);
-                cp_async_word(reinterpret_cast<float*>(reinterpret_cast<uint4*>(xsh) + 3 * T) + tid,
+                cp_async_word(reinterpret_cast<float*>(reinterpret_cast<uint4*>(rsh) + 3 * T) + tid,
                               reinterpret_cast<const float*>(reinterpret_cast<const uint4*>(xb) + 3 * g.V) + s);
             }
         }
@@ -154,31 +260,34 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     __syncthreads();
 
     // 2. residual r = v - D x at this site: interior neighbours and every
-    //    forward link from shared memory, boundary neighbours through L2
+    //    forward link from shared memory, boundary neighbours through L2.
+    //    The eight hops are unrolled with compile-time directions so that the
+    //    loads of one hop overlap the arithmetic of the previous one.
     if (act) {
         if (mode != 0) {
             cx<C> acc[12], psi[12], u[9];
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[c] = czero<C>();
             const bool general = (mode == 2);
-#define SAP_RES_HOPS(MU)                                                                     \
+            const char* xsh = reinterpret_cast<const char*>(rsh);
+#define SAP_RES_HOPS(MU, LS_MU)                                                              \
     {                                                                                        \
         if (lx[MU] + 1 < g.b[MU]) {                                                          \
             if (general) {                                                                   \
-                load_spinor<PS, C, false>(xsh, T, tid + lstride[MU], psi);                   \
-                load_link<PL, C, false>(lsh, T, MU, tid, u);                                 \
+                load_spinor<PS, C, false>(xsh, T, tid + LS_MU, psi);                         \
+                LS::template load<C>(lsh, T, MU, tid, u);                                    \
                 hop<MU, +1, C>(psi, u, acc);                                                 \
             }                                                                                \
         } else {                                                                             \
             load_spinor<PS, C>(xb, g.V, neighbour(g, s, xg, MU, +1), psi);                   \
-            load_link<PL, C, false>(lsh, T, MU, tid, u);                                     \
+            LS::template load<C>(lsh, T, MU, tid, u);                                        \
             hop<MU, +1, C>(psi, u, acc);                                                     \
         }                                                                                    \
         if (lx[MU] >= 1) {                                                                   \
             if (general) {                                                                   \
-                const int tn = tid - lstride[MU];                                            \
+                const int tn = tid - LS_MU;                                                  \
                 load_spinor<PS, C, false>(xsh, T, tn, psi);                                  \
-                load_link<PL, C, false>(lsh, T, MU, tn, u);                                  \
+                LS::template load<C>(lsh, T, MU, tn, u);                                     \
                 hop<MU, -1, C>(psi, u, acc);                                                 \
             }                                                                                \
         } else {                                                                             \
@@ -188,10 +297,10 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             hop<MU, -1, C>(psi, u, acc);                                                     \
         }                                                                                    \
     }
-            SAP_RES_HOPS(0)
-            SAP_RES_HOPS(1)
-            SAP_RES_HOPS(2)
-            SAP_RES_HOPS(3)
+            SAP_RES_HOPS(0, 1)
+            SAP_RES_HOPS(1, ls1)
+            SAP_RES_HOPS(2, ls2)
+            SAP_RES_HOPS(3, ls3)
 #undef SAP_RES_HOPS
             const C half = (C)0.5;
             if (general) {
@@ -213,8 +322,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
 
     // 3. MR on D^l y = r^l out of shared memory
     for (int it = 0; it < nmr; ++it) {
-#pragma unroll
-        for (int c = 0; c < 12; ++c) rho_sh[c * T + tid] = rho[c];
+        rho_store<C>(rsh, T, tid, rho);
         __syncthreads();
         cx<C> p[12];
         C pr_re = 0, pr_im = 0, pp = 0;
@@ -222,25 +330,24 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             cx<C> acc[12], psi[12], u[9];
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[c] = czero<C>();
-#define SAP_LOC_HOPS(MU)                                                                      \
+#define SAP_LOC_HOPS(MU, LS_MU)                                                               \
     {                                                                                         \
         if (lx[MU] + 1 < g.b[MU]) {                                                           \
-            const int tn = tid + lstride[MU];                                                 \
-            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];       \
-            load_link<PL, C, false>(lsh, T, MU, tid, u);                                      \
+            rho_load<C>(rsh, T, tid + LS_MU, psi);                                            \
+            LS::template load<C>(lsh, T, MU, tid, u);                                         \
             hop<MU, +1, C>(psi, u, acc);                                                      \
         }                                                                                     \
         if (lx[MU] >= 1) {                                                                    \
-            const int tn = tid - lstride[MU];                                                 \
-            _Pragma("unroll") for (int c = 0; c < 12; ++c) psi[c] = rho_sh[c * T + tn];       \
-            load_link<PL, C, false>(lsh, T, MU, tn, u);                                       \
+            const int tn = tid - LS_MU;                                                       \
+            rho_load<C>(rsh, T, tn, psi);                                                     \
+            LS::template load<C>(lsh, T, MU, tn, u);                                          \
             hop<MU, -1, C>(psi, u, acc);                                                      \
         }                                                                                     \
     }
-            SAP_LOC_HOPS(0)
-            SAP_LOC_HOPS(1)
-            SAP_LOC_HOPS(2)
-            SAP_LOC_HOPS(3)
+            SAP_LOC_HOPS(0, 1)
+            SAP_LOC_HOPS(1, ls1)
+            SAP_LOC_HOPS(2, ls2)
+            SAP_LOC_HOPS(3, ls3)
 #undef SAP_LOC_HOPS
             const C half = (C)0.5;
 #pragma unroll
@@ -282,8 +389,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
 template <int PS, int PL, class C>
 int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U, const int* jtab, int nrhs,
                  int colour, int nmr, int mode, int threads, cudaStream_t st) {
-    typedef typename link_word<PL>::type LW;
-    const size_t smem = sizeof(C) * 24 * threads + sizeof(LW) * 36 * threads + sizeof(C) * 3 * 32;
+    const size_t smem = sizeof(C) * 24 * threads + (size_t)LinkSh<PL>::kBytes * threads + sizeof(C) * 3 * 32;
     // the shared-memory limit is a per-device property of the kernel: set it once per device
     static std::mutex mu;
     static std::set<int> done;
@@ -310,14 +416,14 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
     return DW_OK;
 }
 
-size_t link_word_bytes(int plink) { return plink == P64 ? 16 : plink == P32 ? 8 : 4; }
+size_t link_sh_bytes(int plink) { return plink == P64 ? 576 : plink == P32 ? 288 : 144; }
 
 }  // namespace
 
 int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads) {
     const size_t c = (pspin == P64) ? 8 : 4;
     (void)g;
-    return (int)(c * 24 * threads + link_word_bytes(plink) * 36 * threads + c * 3 * 32);
+    return (int)(c * 24 * threads + link_sh_bytes(plink) * threads + c * 3 * 32);
 }
 
 int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
