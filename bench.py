@@ -151,6 +151,7 @@ def dw_bandwidth(peaks, reps=10):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = {"lattice": list(dims), "l2": "256 MB write before each call", "reps": reps}
     for name, prec in (("f64", dw.DW_F64), ("f32", dw.DW_F32), ("f16", dw.DW_F16)):
+        torch.cuda.nvtx.range_push("dw_apply_" + name)  # lets a profiler select these launches
         dw.dw_apply(ctx, ind, outd, prec)  # builds this precision's link copy
         dw.dw_profile(ctx, True)
         dw.dw_profile_read(ctx, reset=True)
@@ -160,6 +161,7 @@ def dw_bandwidth(peaks, reps=10):
         torch.cuda.synchronize()
         d = dw.dw_profile_read(ctx, reset=True)["dw_" + name]
         dw.dw_profile(ctx, False)
+        torch.cuda.nvtx.range_pop()
         avg_s = d["total_ms"] / d["launches"] / 1e3
         gbs = d["bytes"] / d["launches"] / avg_s / 1e9
         out[name] = {"GB/s": gbs, "frac": gbs / peaks["hbm_gbs"], "avg_us": avg_s * 1e6,
@@ -541,6 +543,7 @@ def main():
     tr = kernel_traffic(dom)
     roof.update({"kernel": dom, "traffic": tr, "launches": d["launches"], "avg_us": 1e3 * avg_ms})
     shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4) for k, v in prof.items()}
+    avg_us = {k: round(1e3 * v["total_ms"] / v["launches"], 2) for k, v in prof.items() if v["launches"]}
     dwbw = None if args.no_dw_bw else dw_bandwidth(peaks)
 
     line = {
@@ -555,6 +558,7 @@ def main():
         "iterations": iters,
         "roofline": roof,
         "kernel_share": shares,
+        "kernel_avg_us": avg_us,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(bh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8)},
         "gpu_launches": int(launches),

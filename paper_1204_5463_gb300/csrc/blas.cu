@@ -124,23 +124,21 @@ struct Elem<PDF> {
 };
 
 // ---- multi-dot: partial[r][blk][i] = <V_i, w> (i < nv), [nvmax] = ||w||^2 ---
-// Each CTA stages a chunk of w in shared memory; warp q owns basis vectors
-// i = q, q + 8, q + 16, ... and sweeps them over the chunk with its lanes, so
-// every V_i element is read once, coalesced, and the warp reductions happen
-// once per CTA at the end.
-constexpr int kDotE = 16;              // elements per thread per range
-constexpr int kDotG = 8;               // basis vectors per CTA
-constexpr int kDotRange = kT * kDotE;  // elements per range (4096)
+// The CTAs of one group of 8 basis vectors split the elements between them
+// (grid stride); each thread reads w[e] once into registers and the 8 V_i[e]
+// of its group, so every V_i element is read once, coalesced, with the loads
+// of two elements (16 words) in flight per thread and no shared-memory
+// staging or barriers in the stream. The warp reductions happen once per CTA
+// at the end.
+constexpr int kDotG = 8;  // basis vectors per CTA
 
-// partial[r][blk][i] over the ranges this CTA sweeps, for its group of 8
+// partial[r][slot][i] over the elements this CTA sweeps, for its group of 8
 // vectors; the CTAs of group 0 also write ||w||^2 and zero the unused slots.
 template <int VP>
 __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
                                                          int nv_off, int nvmax, int ngroups, double2* partial) {
     typedef Elem<VP> E;
     typedef typename E::C C;
-    typedef typename E::T T16;
-    __shared__ T16 ws[kDotRange];
     __shared__ double2 red[kDotG][kT / 32];
     __shared__ double redn[kT / 32];
     const int r = blockIdx.y;
@@ -154,44 +152,25 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
     const int i0 = grp * kDotG;
     const int G = max(0, min(kDotG, nv - i0));  // vectors of this CTA
     const double2* Vr = Vb.base + r * Vb.rhs_stride + (long long)(Vb.col_off + i0) * Vb.col_stride;
-    const T16* wr = reinterpret_cast<const T16*>(w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride);
+    const double2* wr = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
     C acc[kDotG];
 #pragma unroll
     for (int q = 0; q < kDotG; ++q) acc[q] = E::zero();
     typename E::N wacc = E::nzero();
-    const long long nranges = (n + kDotRange - 1) / kDotRange;
-    for (long long rg = slot; rg < nranges; rg += nslots) {
-        const long long e0 = rg * kDotRange;
-        __syncthreads();  // the previous range of w is no longer read
-#pragma unroll
-        for (int k = 0; k < kDotE; ++k) {
-            const long long e = e0 + t + (long long)k * kT;
-            T16 v{};
-            if (e < n) {
-                v = wr[e];
-                if (grp == 0) E::norm2_acc(wacc, E::load_rw(reinterpret_cast<const double2*>(&v), 0));
-            }
-            ws[t + k * kT] = v;
-        }
-        __syncthreads();
-        const bool full = e0 + kDotRange <= n;
-        // element-outer, vector-inner: the G accumulators are independent
-        // dependency chains, and the G loads of one element are in flight together
+    const long long stride = (long long)nslots * kT;
+    // element-outer, vector-inner: the G accumulators are independent
+    // dependency chains, and the G loads of one element are in flight together
 #pragma unroll 2
-        for (int k = 0; k < kDotE; ++k) {
-            const long long e = e0 + t + (long long)k * kT;
-            const T16 wraw = ws[t + k * kT];
-            const C wv = E::load_rw(reinterpret_cast<const double2*>(&wraw), 0);
-            if (full || e < n) {
-                C vv[kDotG];
+    for (long long e = (long long)slot * kT + t; e < n; e += stride) {
+        const C wv = E::load(wr, e);
+        if (grp == 0) E::norm2_acc(wacc, wv);
+        C vv[kDotG];
 #pragma unroll
-                for (int q = 0; q < kDotG; ++q)
-                    if (q < G) vv[q] = E::load(Vr + (long long)q * Vb.col_stride, e);
+        for (int q = 0; q < kDotG; ++q)
+            if (q < G) vv[q] = E::load(Vr + (long long)q * Vb.col_stride, e);
 #pragma unroll
-                for (int q = 0; q < kDotG; ++q)
-                    if (q < G) E::mac_conj(acc[q], vv[q], wv);
-            }
-        }
+        for (int q = 0; q < kDotG; ++q)
+            if (q < G) E::mac_conj(acc[q], vv[q], wv);
     }
     // CTA reduction of the G dot products (warp shuffles, then across warps)
 #pragma unroll
@@ -515,11 +494,12 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
                     double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
     if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
-    // CTAs: (ranges of w) x (groups of 8 vectors); at most nblk range slots
+    // CTAs: (element slots) x (groups of 8 vectors), one wave of two CTAs per
+    // SM per right-hand side; at most nblk slots
     const int ngroups = (nvmax + kDotG - 1) / kDotG;
-    long long nb = (n + kDotRange - 1) / kDotRange;
+    long long nb = (152LL * 2 + ngroups - 1) / ngroups;
     if (nb > nblk) nb = nblk;
-    if (nb * ngroups > 152LL * 2 * 8) nb = (152LL * 2 * 8 + ngroups - 1) / ngroups;
+    if (nb > (n + kT - 1) / kT) nb = (n + kT - 1) / kT;
     if (nb < 1) nb = 1;
     const dim3 grid((unsigned)(nb * ngroups), nrhs);
     if (vp == PDF)

@@ -63,14 +63,19 @@ struct Geom {
     int ndom;      // number of domains
 };
 
+// 32-bit arithmetic: contexts are limited to fewer than 2^31 / 24 sites
 __device__ __forceinline__ void site_coords(const Geom& g, long long s, int x[4]) {
-    long long t = s;
-    x[0] = (int)(t % g.d[0]);
-    t /= g.d[0];
-    x[1] = (int)(t % g.d[1]);
-    t /= g.d[1];
-    x[2] = (int)(t % g.d[2]);
-    x[3] = (int)(t / g.d[2]);
+    unsigned t = (unsigned)s;
+    const unsigned d0 = (unsigned)g.d[0], d1 = (unsigned)g.d[1], d2 = (unsigned)g.d[2];
+    unsigned q = t / d0;
+    x[0] = (int)(t - q * d0);
+    t = q;
+    q = t / d1;
+    x[1] = (int)(t - q * d1);
+    t = q;
+    q = t / d2;
+    x[2] = (int)(t - q * d2);
+    x[3] = (int)q;
 }
 
 __device__ __forceinline__ long long site_index(const Geom& g, const int x[4]) {

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) convert_kernel(FieldRef in, FieldRef
 }
 
 template <int PI, int PO, int PL, class C, bool SUB>
-__global__ void __launch_bounds__(kThreads) dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U,
+__global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? 4 : 1) dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U,
                                                       const int* jtab, int nrhs, FieldRef sub) {
     const int r = blockIdx.x % nrhs;
     const long long s = (blockIdx.x / nrhs) * (long long)blockDim.x + threadIdx.x;
