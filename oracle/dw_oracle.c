@@ -11,17 +11,17 @@
  *   spinor       psi[site][spin 0..3][colour 0..2]          (12 complex / site)
  *   gauge field  U[site][mu 0..3][row 0..2][col 0..2]        (36 complex / site)
  *
- * Operator (Sec. 2, Eq. "Dw"), written with a bare mass m0 instead of kappa:
+ * Operator (Sec. 1, Eq. "Dw"), written with a bare mass m0 instead of kappa:
  *   (D psi)_n = (4+m0) psi_n
  *               - 1/2 sum_j [ (1+gamma_j) U_{n,j} psi_{n+j}
  *                            + (1-gamma_j) U^dagger_{n-j,j} psi_{n-j} ]
  * which equals D_kappa / (2 kappa) with kappa = 1/(2(4+m0)); n +- j is taken
  * modulo d_j (periodic in all four directions).
  *
- * Local operator (Sec. 2, Eq. "Dw_local"): the same sum restricted to hops
+ * Local operator (Sec. 1, Eq. "Dw_local"): the same sum restricted to hops
  * whose both ends lie in the same domain L^l (a 4-D box of block[] sites).
  *
- * SAP (Sec. 2, Algorithm 2): domains are coloured by the parity of the sum of
+ * SAP (Sec. 1, Algorithm 2): domains are coloured by the parity of the sum of
  * their block coordinates; colour 0 (the one containing site 0) is swept first.
  * Each sweep computes r^l = (b - D x)^l with the full operator, approximately
  * solves D^l y^l = r^l, and adds the correction: x^l <- x^l + y^l.
@@ -30,7 +30,7 @@
  *   p = D^l rho;  alpha = <p,rho>/<p,p>  (<a,b> = a^H b);  y += alpha rho;
  *   rho -= alpha p.  nmr == 0 selects an exact solve by Gaussian elimination
  *   with partial pivoting (small domains only), used to pin SAP against the
- *   closed series form of the preconditioner (Sec. 4).
+ *   closed series form of the preconditioner (Sec. 3).
  */
 #include <complex.h>
 #include <math.h>

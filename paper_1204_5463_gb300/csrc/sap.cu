@@ -1,4 +1,4 @@
-// One colour half-sweep of the Schwarz alternating procedure (Sec. 2,
+// One colour half-sweep of the Schwarz alternating procedure (Sec. 1,
 // Algorithm 2) with inexact minimal-residual domain solves (Sec. 3).
 //
 // One CTA owns one domain L^l of the swept colour (and one right-hand side);

@@ -4,11 +4,11 @@
 // per-rhs column table): preconditioning z_j = M v_j (SAP sweeps), the
 // Arnoldi product w = D z_j, classical Gram-Schmidt with selective
 // reorthogonalisation, normalisation. Host side: the (m+1) x m Hessenberg
-// matrix per rhs, its Givens QR (implicit residual, Sec. 4.4), and at each
+// matrix per rhs, its Givens QR (implicit residual, Sec. 4.2 and 4.6), and at each
 // cycle end the least-squares solve, the harmonic Ritz eigenproblem
 // (Lemma 1a) and the QR of G_{k+1} (Eq. "G_kplus1").
 //
-// Refinement scheme of Sec. 4.5: every cycle ends with an explicit FP64
+// Refinement scheme of Sec. 4.7 (Algorithm 5): every cycle ends with an explicit FP64
 // residual r = b - D x. It supplies the last column of G_{k+1} (V_{m+1}^H r),
 // the vector v_{k+1} (r orthonormalised against V_k) and the right-hand side
 // c = [V_{k+1}^H r; 0]; a clean restart (plain first cycle from r) follows
