@@ -254,7 +254,7 @@ def run_serving(args, rank, world):
         nrhs = int(rng.integers(1, 13))
         b = np.ascontiguousarray(fg.gaussian_source(d, 5000 + i, nrhs=nrhs))
         reqs.append(dict(t=t, dims=d, eps=e, m0=m0, delta=delta, nrhs=nrhs, b=b, x=np.zeros_like(b)))
-    srv = dw.dw_server_create(150 << 30, args.slots)
+    srv = dw.dw_server_create(int(150e9), args.slots)  # 150 GB budget
     keep = []
     ids = [None] * len(reqs)
 
@@ -310,7 +310,7 @@ def run_workload(args, rank, world):
     import paper_1204_5463_gb300 as dw
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cfg = dict(fg.lattice_configs()[args.workload])
+    cfg = dict(fg.lattice_configs()[WORKLOAD if args.workload == "sap_standalone" else args.workload])
     dims = cfg["dims"]
     stream = torch.cuda.current_stream()
 
@@ -326,8 +326,10 @@ def run_workload(args, rank, world):
         ctx = dw.dw_create(dims, block, cfg["m0"], stream.cuda_stream)
         try:
             dw.dw_set_gauge(ctx, Ud, True)
-            P = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
-                                     mr_steps=cfg["mr_steps"], nrhs=nrhs, **kw)
+            opts = dict(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                        mr_steps=cfg["mr_steps"], nrhs=nrhs)
+            opts.update(kw)
+            P = dw.dw_default_params(**opts)
             bd = dev(b)
             xd = torch.zeros_like(bd)
             torch.cuda.synchronize()
@@ -339,7 +341,33 @@ def run_workload(args, rank, world):
         finally:
             dw.dw_destroy(ctx)
 
-    if args.workload.startswith("batched"):
+    if args.workload == "sap_standalone":
+        # SAP as a stand-alone solver (the analogue of the paper's Fig. 5): the
+        # relative residual after s cycles from x = 0, for bare masses around
+        # the spectral edge of D (delta = smallest real part of spec D_m0)
+        import fieldgen as fg2
+
+        edge = fg2.spectral_edges()[fg2.edge_key(dims, cfg["eps"], cfg["seed"])]["edge_re"]
+        b = fg.gaussian_source(dims, 1)
+        bd = dev(b)
+        zd = torch.empty_like(bd)
+        rd = torch.empty_like(bd)
+        out["sap_cycles_max"] = args.sap_cycles_max
+        for delta in (0.3, 0.1, 0.03, 0.01, -0.01, -0.03):
+            m0 = delta - edge
+            ctx = dw.dw_create(dims, cfg["block"], m0, stream.cuda_stream)
+            try:
+                dw.dw_set_gauge(ctx, Ud, True)
+                hist = []
+                for s_ in range(1, args.sap_cycles_max + 1):
+                    dw.sap_precondition(ctx, bd, zd, s_, cfg["mr_steps"], dw.DW_F32, 1)
+                    dw.dw_apply(ctx, zd, rd, dw.DW_F64, 1)
+                    hist.append(float(torch.linalg.vector_norm(bd - rd) / torch.linalg.vector_norm(bd)))
+            finally:
+                dw.dw_destroy(ctx)
+            out["runs"].append({"delta": delta, "m0": m0, "kappa": 1.0 / (2.0 * (4.0 + m0)),
+                                "rel_res_by_cycle": hist})
+    elif args.workload.startswith("batched"):
         b = fg.point_sources(dims)
         blocks = [tuple(cfg["block"])]
         if not args.no_tune:
@@ -387,9 +415,11 @@ def main():
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="wilson_16x16x16x32 (default, the benchmark line), batched_24x24x24x48, mixed_32x32x32x64")
+                    help="wilson_16x16x16x32 (default, the benchmark line), batched_24x24x24x48, mixed_32x32x32x64, "
+                         "sap_standalone (SAP as a solver around the spectral edge, 16^3x32)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--k0-cycles", type=int, default=40, help="cycle cap of the restarted FGMRES comparison")
+    ap.add_argument("--sap-cycles-max", type=int, default=30, help="SAP cycles of the stand-alone SAP runs")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -457,12 +487,14 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     lat = []
     iters = []
+    cleans = []
     ev0.record(stream)
     for _ in range(args.steps):
         t0 = time.perf_counter()
         S = dw.fgmresdr_solve(ctx, bd, xd, P)
         lat.append(1e3 * (time.perf_counter() - t0))
         iters.append(S.iterations)
+        cleans.append(S.clean_restarts)
         assert S.converged == 1 and S.true_rel_res[0] <= cfg["tol"]
     ev1.record(stream)
     barrier()
@@ -526,6 +558,33 @@ def main():
               "true_rel_res_max": max(S12.true_rel_res[i] for i in range(12)), "ratio_vs_plain": mb_value / value}
         del b12d, x12d
 
+    # the paper's single-precision Arnoldi process with double-float refinement
+    # per cycle (FP32 basis), same lattice, rhs and solver parameters
+    sp32 = None
+    if not args.no_batched:
+        P32 = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                                   mr_steps=cfg["mr_steps"], sap_prec=dw.PREC[args.sap_prec], matvec_prec=dw.DW_F32,
+                                   outer_prec=dw.DW_F32)
+        S32 = dw.fgmresdr_solve(ctx, bd, xd, P32)
+        barrier()
+        s0e, s1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0e.record(stream)
+        for _ in range(args.steps):
+            S32 = dw.fgmresdr_solve(ctx, bd, xd, P32)
+            assert S32.converged == 1 and S32.true_rel_res[0] <= cfg["tol"]
+        s1e.record(stream)
+        barrier()
+        sms = s0e.elapsed_time(s1e)
+        if dist:
+            t = torch.tensor([sms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sms = float(t.item())
+        sv = args.steps * world / (sms / 1e3)
+        sp32 = {"value": sv, "unit": "solves/s", "outer_prec": "f32 basis, double-float x/b/r",
+                "ms_per_step": sms / args.steps, "iterations": S32.iterations, "cycles": S32.cycles,
+                "clean_restarts": S32.clean_restarts, "true_rel_res": S32.true_rel_res[0],
+                "ratio_vs_plain": sv / value}
+
     # roofline of the dominant kernel class of the step
     peaks, peak_src = measured_peaks()
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
@@ -556,6 +615,7 @@ def main():
                    "l2": "working set > L2 (Krylov basis ~0.8 GB)"},
         "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)), "min": min(lat)},
         "iterations": iters,
+        "clean_restarts": cleans,
         "roofline": roof,
         "kernel_share": shares,
         "kernel_avg_us": avg_us,
@@ -564,6 +624,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "mixed_batched": mb,
+        "fp32_arnoldi": sp32,
         "dw_apply": dwbw,
     }
     if rank == 0 and not args.no_cpu_baseline:

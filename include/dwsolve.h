@@ -119,8 +119,12 @@ typedef struct {
     int nrhs;               /* right-hand sides solved together, 1..DW_MAX_RHS             */
     int host_buffers;       /* 1: b and x are host pointers (copies inside the call)       */
     int use_x0;             /* 1: x holds the initial guess; 0: x0 = 0                     */
-    dw_prec outer_prec;     /* outer vectors V, x, b, r and their Gram-Schmidt / update
-                               arithmetic: DW_F64 or DW_DF64 (default)                     */
+    dw_prec outer_prec;     /* outer vectors and their Gram-Schmidt / update arithmetic:
+                               DW_F64 (V, x, b, r in FP64), DW_DF64 (default: double-float),
+                               or DW_F32: the single-precision Arnoldi process of Sec. 4.7
+                               (V and all basis arithmetic in FP32, x, b, r and the
+                               explicit residual double-float; needs sap_prec F32/F16/BF16
+                               and matvec_prec DW_F32)                                      */
 } dw_solver_params;
 
 typedef struct {
@@ -141,7 +145,8 @@ void dw_default_params(dw_solver_params* P);
 
 /* Solve D x = b for nrhs right-hand sides with FGMRES-DR (Algorithm 4):
  * flexible Arnoldi (Algorithm 3) with classical Gram-Schmidt and selective
- * reorthogonalisation in FP64, Givens-updated implicit residual (Sec. 4.2, 4.6),
+ * reorthogonalisation in the basis precision (outer_prec), Givens-updated
+ * implicit residual (Sec. 4.2, 4.6),
  * harmonic Ritz deflation (Lemma 1a, Eqs. "G_kplus1", "hatHk"), and the
  * refinement scheme of Sec. 4.7 (Algorithm 5): every cycle recomputes r = b - D x in FP64 and
  * injects it into the least-squares right-hand side, the last column of

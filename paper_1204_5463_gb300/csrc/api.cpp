@@ -296,7 +296,10 @@ int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_para
     if (P->matvec_prec != DW_F64 && P->matvec_prec != DW_F32)
         return fail(DW_EINVAL, "matvec_prec must be DW_F64 or DW_F32");
     if (P->nrhs < 1 || P->nrhs > DW_MAX_RHS) return fail(DW_EINVAL, "nrhs out of range");
-    if (P->outer_prec != DW_F64 && P->outer_prec != DW_DF64) return fail(DW_EINVAL, "outer_prec must be DW_F64 or DW_DF64");
+    if (P->outer_prec != DW_F64 && P->outer_prec != DW_DF64 && P->outer_prec != DW_F32)
+        return fail(DW_EINVAL, "outer_prec must be DW_F64, DW_DF64 or DW_F32");
+    if (P->outer_prec == DW_F32 && (P->sap_prec == DW_F64 || P->matvec_prec != DW_F32))
+        return fail(DW_EINVAL, "an FP32 Arnoldi basis needs a 32- or 16-bit SAP and an FP32 matvec");
     if (!(P->clean_restart_t > 1.0)) return fail(DW_EINVAL, "clean_restart_t must be > 1");
     return solve(ctx, b, x, P, S);
 }

@@ -76,6 +76,58 @@ struct Elem<P64> {
     static __device__ __forceinline__ C add(C a, C b) { return C{a.re + b.re, a.im + b.im}; }
 };
 
+// FP32 basis vectors (the single-precision Arnoldi process of Sec. 4.7): one
+// float2 per complex element, in the S32 spinor layout (float4[6][V], two
+// complex per site and plane). Dot products and updates are element-wise, so
+// they never depend on which complex element sits where; the per-site
+// normalisation uses the spinor layout explicitly. Products accumulate in
+// FP32 per thread and in FP64 across threads.
+template <>
+struct Elem<P32> {
+    typedef float2 T;
+    struct C {
+        float re, im;
+    };
+    static __device__ __forceinline__ C load(const double2* p, long long e) {
+        const float2 v = __ldg(&reinterpret_cast<const float2*>(p)[e]);
+        return C{v.x, v.y};
+    }
+    static __device__ __forceinline__ C load_rw(const double2* p, long long e) {
+        const float2 v = reinterpret_cast<const float2*>(p)[e];
+        return C{v.x, v.y};
+    }
+    static __device__ __forceinline__ void store(double2* p, long long e, C v) {
+        reinterpret_cast<float2*>(p)[e] = make_float2(v.re, v.im);
+    }
+    static __device__ __forceinline__ C zero() { return C{0.f, 0.f}; }
+    static __device__ __forceinline__ void mac_conj(C& acc, C a, C b) {
+        acc.re = fmaf(a.re, b.re, acc.re);
+        acc.re = fmaf(a.im, b.im, acc.re);
+        acc.im = fmaf(a.re, b.im, acc.im);
+        acc.im = fmaf(-a.im, b.re, acc.im);
+    }
+    static __device__ __forceinline__ void mac(C& acc, C h, C a) {
+        acc.re = fmaf(h.re, a.re, acc.re);
+        acc.re = fmaf(-h.im, a.im, acc.re);
+        acc.im = fmaf(h.re, a.im, acc.im);
+        acc.im = fmaf(h.im, a.re, acc.im);
+    }
+    typedef float N;
+    static __device__ __forceinline__ N nzero() { return 0.f; }
+    static __device__ __forceinline__ void norm2_acc(N& s, C a) { s = fmaf(a.re, a.re, fmaf(a.im, a.im, s)); }
+    static __device__ __forceinline__ double nfin(N s) { return (double)s; }
+    static __device__ __forceinline__ C fin(C a) { return a; }
+    static __device__ __forceinline__ double2 to_d2(C a) { return make_double2((double)a.re, (double)a.im); }
+    static __device__ __forceinline__ C from_d2(double2 a) { return C{(float)a.x, (float)a.y}; }
+    // reduced in FP64: the per-thread FP32 partial sums are converted first
+    static __device__ __forceinline__ double2 warp_reduce_d(C a) {
+        return make_double2(warp_sum((double)a.re), warp_sum((double)a.im));
+    }
+    static __device__ __forceinline__ C scale(C a, float s) { return C{a.re * s, a.im * s}; }
+    static __device__ __forceinline__ cx<float> to_f(C a) { return mk<float>(a.re, a.im); }
+    static __device__ __forceinline__ C add(C a, C b) { return C{a.re + b.re, a.im + b.im}; }
+};
+
 template <>
 struct Elem<PDF> {
     typedef float4 T;
@@ -176,8 +228,12 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
 #pragma unroll
     for (int q = 0; q < kDotG; ++q)
         if (q < G) {
-            const C sq = E::warp_reduce(acc[q]);
-            if (lane == 0) red[q][warp] = E::to_d2(sq);
+            double2 sq;
+            if constexpr (VP == P32)
+                sq = E::warp_reduce_d(acc[q]);
+            else
+                sq = E::to_d2(E::warp_reduce(acc[q]));
+            if (lane == 0) red[q][warp] = sq;
         }
     const double wn = (grp == 0) ? warp_sum(E::nfin(wacc)) : 0.0;
     if (lane == 0) redn[warp] = wn;
@@ -288,12 +344,24 @@ __global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, lon
     const double2* src = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
     double2* out = dst.base + r * dst.rhs_stride + (long long)(j + dst.col_off) * dst.col_stride;
     cx<CL> f[12];
+    if constexpr (VP == P32) {  // S32 spinor layout, scaled in FP32
+        cx<float> q[12];
+        load_spinor<P32, float, true>(reinterpret_cast<const char*>(src), V, s, q);
+        const float fi = (float)inv;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) q[c] = mk<float>(q[c].re * fi, q[c].im * fi);
+        store_spinor<P32, float>(reinterpret_cast<char*>(out), V, s, q);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) f[c] = mk<CL>((CL)q[c].re, (CL)q[c].im);
+        if constexpr (PS >= 0) store_spinor<PS, CL>(field_ptr(low, jtab, r), V, s, f);
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
         C v;
         if constexpr (VP == PDF)
             v = E::scale(E::load_rw(src, c * V + s), df_from_double(inv));
-        else
+        else if constexpr (VP == P64)
             v = E::scale(E::load_rw(src, c * V + s), inv);
         E::store(out, c * V + s, v);
         const double2 d = E::to_d2(v);
@@ -485,6 +553,7 @@ unsigned grid_for(long long n) {
 }
 
 bool outer_ok(int vp) { return vp == P64 || vp == PDF; }
+bool basis_ok(int vp) { return vp == P64 || vp == PDF || vp == P32; }
 
 }  // namespace
 
@@ -493,7 +562,7 @@ int blas_nblk(long long n) { return (int)grid_for(n); }
 int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
                     double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
-    if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
     // CTAs: (element slots) x (groups of 8 vectors), one wave of two CTAs per
     // SM per right-hand side; at most nblk slots
     const int ngroups = (nvmax + kDotG - 1) / kDotG;
@@ -504,6 +573,8 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
     const dim3 grid((unsigned)(nb * ngroups), nrhs);
     if (vp == PDF)
         multidot_kernel<PDF><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+    else if (vp == P32)
+        multidot_kernel<P32><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     else
         multidot_kernel<P64><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     DW_LAUNCH_CHECK();
@@ -515,9 +586,11 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
 int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs,
                      const double2* coef, int coef_ld, double2* partial, int nblk, double* out_norm2,
                      cudaStream_t st) {
-    if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
     if (vp == PDF)
         multiaxpy_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
+    else if (vp == P32)
+        multiaxpy_kernel<P32><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
     else
         multiaxpy_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
     DW_LAUNCH_CHECK();
@@ -528,7 +601,7 @@ int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, 
 
 int launch_normalize(int vp, VecRef w, VecRef dst, long long V, const int* jtab, int nrhs, const double* norm2,
                      int plow, FieldRef low, cudaStream_t st) {
-    if (!outer_ok(vp)) return fail(DW_EINVAL, "bad outer precision");
+    if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
     dim3 grid((unsigned)((V + kT - 1) / kT), nrhs);
 #define NORM(A, B)                                                                                      \
     if (vp == A && plow == B) {                                                                         \
@@ -546,6 +619,10 @@ int launch_normalize(int vp, VecRef w, VecRef dst, long long V, const int* jtab,
     NORM(PDF, P32)
     NORM(PDF, P16)
     NORM(PDF, PB16)
+    NORM(P32, -1)
+    NORM(P32, P32)
+    NORM(P32, P16)
+    NORM(P32, PB16)
 #undef NORM
     return fail(DW_EINVAL, "unsupported normalisation precision combination");
 }

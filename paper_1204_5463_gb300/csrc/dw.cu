@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) convert_kernel(FieldRef in, FieldRef
 }
 
 template <int PI, int PO, int PL, class C, bool SUB>
-__global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? 4 : 1) dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U,
+__global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? ((PI == P32) ? 4 : 3) : 1) dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U,
                                                       const int* jtab, int nrhs, FieldRef sub) {
     const int r = blockIdx.x % nrhs;
     const long long s = (blockIdx.x / nrhs) * (long long)blockDim.x + threadIdx.x;
@@ -240,6 +240,8 @@ int launch_convert(int pin, int pout, FieldRef in, FieldRef out, long long V, co
     CONV(P32, P64)
     CONV(P16, P64)
     CONV(PB16, P64)
+    CONV(P16, P32)
+    CONV(PB16, P32)
     CONV(PDF, P32)
     CONV(PDF, P16)
     CONV(PDF, PB16)
@@ -259,6 +261,8 @@ int launch_dw(int pin, int pout, int plink, const Geom& g, double m0, FieldRef i
     DWC(P32, P32, P32, float)
     DWC(P16, P16, P16, float)
     DWC(PB16, PB16, PB16, float)
+    DWC(P16, P32, P32, float)
+    DWC(PB16, P32, P32, float)
     DWC(P32, P64, P32, float)
     DWC(P16, P64, P32, float)
     DWC(PB16, P64, P32, float)

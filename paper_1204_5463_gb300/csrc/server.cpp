@@ -70,13 +70,19 @@ size_t request_bytes(const dw_request* q) {
     for (int j = 0; j < 4; ++j) V *= q->lattice.dims[j];
     const dw_solver_params& P = q->params;
     const int sp = (int)P.sap_prec;
+    const bool half = (sp == dwk::P16 || sp == dwk::PB16);
     const long long sb = dwk::spinor_bytes(sp, V);
-    const long long fb = 192 * V;
+    const long long zb = (half && P.k > 0) ? dwk::spinor_bytes(dwk::P32, V) : sb;  // Z basis vector
+    const long long fb = 192 * V;                                                  // x, b, r
+    const long long fv = (P.outer_prec == DW_F32) ? 96 * V : fb;                   // Arnoldi basis vector
     long long gauge = dwk::link_bytes(dwk::P64, V) + 576 * V;  // FP64 links + upload staging
     gauge += dwk::link_bytes(dwk::P32, V);                       // Arnoldi product
-    if (sp == dwk::P16 || sp == dwk::PB16) gauge += dwk::link_bytes(sp, V);
-    const long long per_rhs = (long long)(P.m + 1) * fb + (long long)P.m * sb + 3 * fb + sb + 24 * 8 * V;
-    return (size_t)(gauge + (long long)P.nrhs * per_rhs + (long long)(P.k > 0 ? P.k : 1) * sb + (8LL << 20));
+    if (half) gauge += dwk::link_bytes(sp, V);
+    if (P.outer_prec != DW_F64) gauge += 576 * V;  // double-float links of the residual stencil
+    long long per_rhs = (long long)(P.m + 1) * fv + (long long)P.m * zb + 3 * fb + sb + 24 * 8 * V;
+    if (zb != sb) per_rhs += sb;  // SAP output before widening
+    if (fv != fb) per_rhs += fv;  // FP32 copy of the residual
+    return (size_t)(gauge + (long long)P.nrhs * per_rhs + (long long)(P.k > 0 ? P.k : 1) * zb + (8LL << 20));
 }
 
 bool same_field(const CachedCtx& c, const dw_request& r) {

@@ -13,6 +13,20 @@
 // the vector v_{k+1} (r orthonormalised against V_k) and the right-hand side
 // c = [V_{k+1}^H r; 0]; a clean restart (plain first cycle from r) follows
 // when ||r|| / ||r_implicit|| > t.
+//
+// The Arnoldi basis V is kept either in the format of x, b, r (FP64 or
+// double-float) or, as in the single-precision scheme of Sec. 4.7, in FP32
+// (outer_prec = DW_F32): then the whole Arnoldi process, the deflated restart
+// and the least-squares right-hand side run on FP32 vectors, while x, b and
+// the explicit residual stay double-float, so every cycle refines the
+// solution with a residual computed in high precision.
+//
+// The preconditioned vectors Z are kept in the SAP storage format, except
+// that 16-bit SAP storage with deflation (k > 0) keeps Z in FP32: a deflated
+// restart rotates Z_k = Z_m Q_k, and rounding the rotated vectors to 16 bits
+// would break A Z_k = V_{k+1} Hhat_k at the 1e-3 level, so the implicit and
+// explicit residuals would part and force clean restarts. Without rotation
+// any stored z_j is consistent with its own product w = D z_j.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -45,14 +59,18 @@ struct Solver {
     cudaStream_t st;
     Geom g;
     long long V, n;
-    int nrhs, m, k, sp, mp, op;  // op: format of the outer vectors (P64 or PDF)
+    int nrhs, m, k, sp, mp, op;  // op: format of x, b, r (P64 or PDF)
+    int vp;             // format of the Arnoldi basis V (op, or P32)
+    int zp;             // format of the preconditioned basis Z (sp, or P32)
     long long sb;       // bytes of one spinor field in SAP storage
-    long long fb;       // bytes of one FP64 internal field
+    long long zb;       // bytes of one Z vector
+    long long fb;       // bytes of one field in format op
+    long long fv;       // bytes of one basis vector in format vp
     int NP;             // multi-dot row length (m + 2)
     int nblk;
     const char *U_sap, *U_mv, *U64;
     // device buffers (owned by the workspace of the context)
-    char *Vb, *Zb, *xb, *bb, *rb, *vlow, *zscr;
+    char *Vb, *Zb, *xb, *bb, *rb, *vlow, *zscr, *rlow, *zsap;
     double2 *partial, *dots, *Qd, *etad;
     double *norm2d, *scal_d;
     int *jtab_d, *nz_d;
@@ -67,13 +85,28 @@ struct Solver {
 
     int lin(size_t r, int i) const { return (int)(r * NP + i); }
 
-    VecRef vref_all(int r_off, int col_off) const {
+    VecRef vref_all(int r_off, int col_off) const {  // strides in 16-byte units
         VecRef v;
-        v.base = reinterpret_cast<double2*>(Vb) + (long long)r_off * (m + 1) * n;
-        v.rhs_stride = (long long)(m + 1) * n;
-        v.col_stride = n;
+        v.base = reinterpret_cast<double2*>(Vb + (long long)r_off * (m + 1) * fv);
+        v.rhs_stride = (long long)(m + 1) * fv / 16;
+        v.col_stride = fv / 16;
         v.col_off = col_off;
         return v;
+    }
+    // the explicit residual of rhs r as seen by the basis: rb itself, or its
+    // FP32 copy when the basis is FP32
+    VecRef res_vec(int r_off) const {
+        VecRef v;
+        v.base = reinterpret_cast<double2*>((vp == op ? rb : rlow) + (long long)r_off * fv);
+        v.rhs_stride = fv / 16;
+        v.col_stride = 0;
+        v.col_off = 0;
+        return v;
+    }
+    int residual_to_basis(int r) {  // rlow[r] = r in FP32 (no-op for a high-precision basis)
+        if (vp == op) return DW_OK;
+        FieldRef in{rb + (long long)r * fb, 0, 0, 0}, out{rlow + (long long)r * fv, 0, 0, 0};
+        return launch_convert(op, vp, in, out, V, nullptr, 1, st);
     }
     VecRef field_vec(char* base, int r_off) const {
         VecRef v;
@@ -100,7 +133,7 @@ struct Solver {
 
 // Workspace kept by the context between solves (grown on demand).
 struct Workspace {
-    DevBuf V, Z, x, b, r, vlow, zscr, partial, dots, Q, eta, norm2, scal, jtab, nz, canon;
+    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, norm2, scal, jtab, nz, canon;
     double2* dots_h = nullptr;
     double* norm2_h = nullptr;
     int* jtab_h = nullptr;
@@ -119,7 +152,7 @@ static Workspace* workspace_of(dw_ctx* ctx) {
         ctx->ws = new (std::nothrow) Workspace();
         if (ctx->ws)
             for (DevBuf* b : {&ctx->ws->V, &ctx->ws->Z, &ctx->ws->x, &ctx->ws->b, &ctx->ws->r, &ctx->ws->vlow,
-                              &ctx->ws->zscr, &ctx->ws->partial, &ctx->ws->dots, &ctx->ws->Q, &ctx->ws->eta,
+                              &ctx->ws->zscr, &ctx->ws->rlow, &ctx->ws->zsap, &ctx->ws->partial, &ctx->ws->dots, &ctx->ws->Q, &ctx->ws->eta,
                               &ctx->ws->norm2, &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon})
                 b->st = ctx->stream;
     }
@@ -137,9 +170,13 @@ int Solver::setup() {
     k = P.k;
     sp = (int)P.sap_prec;
     mp = (int)P.matvec_prec;
-    op = (P.outer_prec == DW_DF64) ? PDF : P64;
+    op = (P.outer_prec == DW_F64) ? P64 : PDF;
+    vp = (P.outer_prec == DW_F32) ? P32 : op;
+    zp = (k > 0 && (sp == P16 || sp == PB16)) ? P32 : sp;
     sb = spinor_bytes(sp, V);
+    zb = spinor_bytes(zp, V);
     fb = spinor_bytes(op, V);
+    fv = spinor_bytes(vp, V);
     NP = m + 2;
     nblk = blas_nblk(n);
     int rc;
@@ -149,13 +186,15 @@ int Solver::setup() {
     if ((rc = gauge_for(ctx, op == PDF ? PDF : P64, &U64))) return rc;
     Workspace* W = workspace_of(ctx);
     if (!W) return fail(DW_ENOMEM, "workspace allocation failed");
-    if ((rc = W->V.ensure((size_t)nrhs * (m + 1) * fb))) return rc;
-    if ((rc = W->Z.ensure((size_t)nrhs * m * sb))) return rc;
+    if ((rc = W->V.ensure((size_t)nrhs * (m + 1) * fv))) return rc;
+    if ((rc = W->Z.ensure((size_t)nrhs * m * zb))) return rc;
+    if (zp != sp && (rc = W->zsap.ensure((size_t)nrhs * sb))) return rc;
     if ((rc = W->x.ensure((size_t)nrhs * fb))) return rc;
     if ((rc = W->b.ensure((size_t)nrhs * fb))) return rc;
     if ((rc = W->r.ensure((size_t)nrhs * fb))) return rc;
     if ((rc = W->vlow.ensure((size_t)nrhs * sb))) return rc;
-    if ((rc = W->zscr.ensure((size_t)(k > 0 ? k : 1) * sb))) return rc;
+    if (vp != op && (rc = W->rlow.ensure((size_t)nrhs * fv))) return rc;
+    if ((rc = W->zscr.ensure((size_t)(k > 0 ? k : 1) * zb))) return rc;
     if ((rc = W->partial.ensure((size_t)nrhs * nblk * NP * sizeof(double2)))) return rc;
     if ((rc = W->dots.ensure((size_t)2 * nrhs * NP * sizeof(double2)))) return rc;
     if ((rc = W->Q.ensure((size_t)(m + 1) * (m + 1) * sizeof(double2)))) return rc;
@@ -183,6 +222,8 @@ int Solver::setup() {
     rb = W->r.as<char>();
     vlow = W->vlow.as<char>();
     zscr = W->zscr.as<char>();
+    zsap = (zp != sp) ? W->zsap.as<char>() : nullptr;
+    rlow = (vp != op) ? W->rlow.as<char>() : nullptr;
     partial = W->partial.as<double2>();
     dots = W->dots.as<double2>();
     Qd = W->Q.as<double2>();
@@ -212,10 +253,11 @@ int Solver::start_plain(int r) {
     const double nn = s.rnorm * s.rnorm;
     DW_CUDA_TRY(cudaMemcpyAsync(scal_d + r, &nn, sizeof(double), cudaMemcpyHostToDevice, st));
     int rc;
+    if ((rc = residual_to_basis(r))) return rc;
     {
-        ProfScope ps(&ctx->prof, "normalize", 2.0 * fb + sb);
+        ProfScope ps(&ctx->prof, "normalize", 2.0 * fv + sb);
         const FieldRef low{vlow + (long long)r * sb, 0, 0, 0};
-        if ((rc = launch_normalize(op, field_vec(rb, r), vref_all(r, 0), V, nullptr, 1, scal_d + r, sp, low, st)))
+        if ((rc = launch_normalize(vp, res_vec(r), vref_all(r, 0), V, nullptr, 1, scal_d + r, sp, low, st)))
             return rc;
     }
     std::fill(s.H.begin(), s.H.end(), zd(0));
@@ -249,10 +291,11 @@ int Solver::start_deflated(int r) {
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return std::abs(lam[a]) < std::abs(lam[b]); });
     // last column of G_{k+1}: the explicit residual in the old basis, V_{m+1}^H r
+    if ((rc = residual_to_basis(r))) return rc;
     {
-        ProfScope ps(&ctx->prof, "multidot", (double)(mm + 2) * fb);
-        if ((rc = launch_multidot(op, vref_all(r, 0), field_vec(rb, r), n, nullptr, mm + 1, m + 1, 1, partial, nblk,
-                                  dots, st)))
+        ProfScope ps(&ctx->prof, "multidot", (double)(mm + 2) * fv);
+        if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, mm + 1, m + 1, 1, partial, nblk, dots,
+                                  st)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * NP, cudaMemcpyDeviceToHost, st));
@@ -286,39 +329,39 @@ int Solver::start_deflated(int r) {
             Qh[(size_t)i * (m + 1) + c] = make_double2(Q[(size_t)i * k1 + c].real(), Q[(size_t)i * k1 + c].imag());
     DW_CUDA_TRY(cudaMemcpyAsync(Qd, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice, st));
     {
-        ProfScope ps(&ctx->prof, "rotate_V", (double)(mm + 1 + k1) * fb);
-        if ((rc = launch_rotate(op, Vb + (long long)r * (m + 1) * fb, 0, fb, V, 1, nullptr, mm + 1, k1, Qd, m + 1,
+        ProfScope ps(&ctx->prof, "rotate_V", (double)(mm + 1 + k1) * fv);
+        if ((rc = launch_rotate(vp, Vb + (long long)r * (m + 1) * fv, 0, fv, V, 1, nullptr, mm + 1, k1, Qd, m + 1,
                                 nullptr, st)))
             return rc;
     }
     {
-        ProfScope ps(&ctx->prof, "rotate_Z", (double)(mm + k) * sb);
-        if ((rc = launch_rotate(sp, Zb + (long long)r * m * sb, 0, sb, V, 1, nullptr, mm, k, Qd, m + 1, zscr, st)))
+        ProfScope ps(&ctx->prof, "rotate_Z", (double)(mm + k) * zb);
+        if ((rc = launch_rotate(zp, Zb + (long long)r * m * zb, 0, zb, V, 1, nullptr, mm, k, Qd, m + 1, zscr, st)))
             return rc;
     }
     // v_{k+1}: explicit residual orthonormalised against V_k (two CGS passes)
-    double2* Vr = reinterpret_cast<double2*>(Vb) + (long long)r * (m + 1) * n;
-    DW_CUDA_TRY(cudaMemcpyAsync(Vr + (long long)k * n, reinterpret_cast<double2*>(rb) + (long long)r * n,
-                                fb, cudaMemcpyDeviceToDevice, st));
+    char* Vr = Vb + (long long)r * (m + 1) * fv;
+    DW_CUDA_TRY(cudaMemcpyAsync(Vr + (long long)k * fv, reinterpret_cast<char*>(res_vec(r).base), fv,
+                                cudaMemcpyDeviceToDevice, st));
     for (int pass = 0; pass < 2; ++pass) {
-        ProfScope ps(&ctx->prof, "cgs", (double)(2 * k + 3) * fb);
+        ProfScope ps(&ctx->prof, "cgs", (double)(2 * k + 3) * fv);
         VecRef w = vref_all(r, k);
-        if ((rc = launch_multidot(op, vref_all(r, 0), w, n, nullptr, k, m + 1, 1, partial, nblk, dots, st)))
+        if ((rc = launch_multidot(vp, vref_all(r, 0), w, n, nullptr, k, m + 1, 1, partial, nblk, dots, st)))
             return rc;
-        if ((rc = launch_multiaxpy(op, vref_all(r, 0), w, n, nullptr, k, 1, dots, NP, partial, nblk, norm2d + r,
+        if ((rc = launch_multiaxpy(vp, vref_all(r, 0), w, n, nullptr, k, 1, dots, NP, partial, nblk, norm2d + r,
                                    st)))
             return rc;
     }
     {
-        ProfScope ps(&ctx->prof, "normalize", 2.0 * fb);
+        ProfScope ps(&ctx->prof, "normalize", 2.0 * fv);
         VecRef w = vref_all(r, k);
         const FieldRef low{vlow + (long long)r * sb, 0, 0, 0};
-        if ((rc = launch_normalize(op, w, w, V, nullptr, 1, norm2d + r, sp, low, st))) return rc;
+        if ((rc = launch_normalize(vp, w, w, V, nullptr, 1, norm2d + r, sp, low, st))) return rc;
     }
     // c = [V_{k+1}^H r; 0]
     {
-        ProfScope ps(&ctx->prof, "multidot", (double)(k1 + 1) * fb);
-        if ((rc = launch_multidot(op, vref_all(r, 0), field_vec(rb, r), n, nullptr, k1, m + 1, 1, partial, nblk, dots,
+        ProfScope ps(&ctx->prof, "multidot", (double)(k1 + 1) * fv);
+        if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, k1, m + 1, 1, partial, nblk, dots,
                                   st)))
             return rc;
     }
@@ -353,8 +396,8 @@ int Solver::cycle_end(int r) {
     DW_CUDA_TRY(cudaMemcpyAsync(etad, eh.data(), sizeof(double2) * mm, cudaMemcpyHostToDevice, st));
     DW_CUDA_TRY(cudaMemcpyAsync(nz_d, &mm, sizeof(int), cudaMemcpyHostToDevice, st));
     {
-        ProfScope ps(&ctx->prof, "xupdate", (double)mm * sb + 2.0 * fb);
-        if ((rc = launch_xupdate(sp, op, Zb + (long long)r * m * sb, 0, sb,
+        ProfScope ps(&ctx->prof, "xupdate", (double)mm * zb + 2.0 * fb);
+        if ((rc = launch_xupdate(zp, op, Zb + (long long)r * m * zb, 0, zb,
                                  reinterpret_cast<double2*>(xb) + (long long)r * n, 0, V, 1, nz_d, etad, 0, st)))
             return rc;
     }
@@ -405,9 +448,10 @@ int Solver::step() {
     }
     if (nact == 0) return fail(DW_EBREAKDOWN, "no right-hand side left to step");
     DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-    const FieldRef Vf1{Vb, (m + 1) * fb, fb, 1};
-    const FieldRef Zf{Zb, m * sb, sb, 0};
+    const FieldRef Vf1{Vb, (m + 1) * fv, fv, 1};
+    const FieldRef Zf{Zb, m * zb, zb, 0};
     const FieldRef Lf{vlow, sb, 0, 0};
+    const FieldRef Zs = (zp == sp) ? Zf : FieldRef{zsap, sb, 0, 0};  // where the SAP writes z_j
     // z_j = M v_j  (v_j was written in SAP storage to vlow when it was normalised)
     for (int cyc = 0; cyc < P.sap_cycles; ++cyc)
         for (int colour = 0; colour < 2; ++colour) {
@@ -415,15 +459,19 @@ int Solver::step() {
             const double bytes = (double)nact * 0.5 * (2.0 * sb + (mode == 2 ? sb : 0) + link_bytes(sp, V));
             ProfScope ps(&ctx->prof, "sap_sweep", bytes);
             const int thr = (ctx->sap_threads.size() > (size_t)sp) ? ctx->sap_threads[sp] : 0;
-            if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zf, U_sap, jtab_d, nrhs, colour, P.mr_steps, mode, thr,
+            if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zs, U_sap, jtab_d, nrhs, colour, P.mr_steps, mode, thr,
                                        st)))
                 return rc;
         }
+    if (zp != sp) {
+        ProfScope ps(&ctx->prof, "z_widen", (double)nact * (sb + zb));
+        if ((rc = launch_convert(sp, zp, Zs, Zf, V, jtab_d, nrhs, st))) return rc;
+    }
     // w = D z_j  (written into column j+1 of V)
     {
         const int pl = (mp == P64) ? P64 : P32;
-        ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(sp, op, pl, V));
-        if ((rc = launch_dw(sp, op, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st))) return rc;
+        ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(zp, vp, pl, V));
+        if ((rc = launch_dw(zp, vp, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st))) return rc;
     }
     // classical Gram-Schmidt: h = V^H w, w' = w - V h; a second projection
     // ("twice is enough") only where cancellation could cost orthogonality at
@@ -432,21 +480,25 @@ int Solver::step() {
     for (int r = 0; r < nrhs; ++r)
         if (jtab_h[r] >= 0) jsum += jtab_h[r] + 1;
     {
-        ProfScope ps(&ctx->prof, "cgs_project", (jsum + nact) * fb);
-        if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
+        ProfScope ps(&ctx->prof, "cgs_project", (jsum + nact) * fv);
+        if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
                                   st)))
             return rc;
     }
     {
-        ProfScope ps(&ctx->prof, "cgs_update", (jsum + 2.0 * nact) * fb);
-        if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
+        ProfScope ps(&ctx->prof, "cgs_update", (jsum + 2.0 * nact) * fv);
+        if ((rc = launch_multiaxpy(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
                                    norm2d, st)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
     DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     if ((rc = sync())) return rc;
-    const double unit = (op == PDF) ? 3.552713678800501e-15 : 1.1102230246251565e-16;
+    // unit roundoff of the basis format, and the orthogonality level below
+    // which a second pass is taken (FP64-class: 1e-13; FP32: 1e-5)
+    const double unit = (vp == P32) ? 5.960464477539063e-08 : (vp == PDF) ? 3.552713678800501e-15
+                                                                            : 1.1102230246251565e-16;
+    const double tau = (vp == P32) ? 1e-5 : 1e-13;
     std::vector<std::vector<zd>> h(nrhs);
     bool need2 = false;
     for (int r = 0; r < nrhs; ++r) {
@@ -456,7 +508,7 @@ int Solver::step() {
         for (int i = 0; i <= j; ++i) h[r][i] = zd(dots_h[lin(r, i)].x, dots_h[lin(r, i)].y);
         R[r].wn0 = std::sqrt(dots_h[lin(r, m + 1)].x);
         const double ratio = std::sqrt(norm2_h[r]) / (R[r].wn0 > 0 ? R[r].wn0 : 1.0);
-        const bool re = unit > 1e-13 * ratio;
+        const bool re = unit > tau * ratio;
         need2 |= re;
         if (!re) jtab_h[r] = -1;
     }
@@ -468,11 +520,11 @@ int Solver::step() {
             if (jtab_h[r] >= 0) js2 += jtab_h[r] + 1, ++n2;
         std::vector<double> keep(norm2_h, norm2_h + nrhs);
         {
-            ProfScope ps(&ctx->prof, "cgs_reorth", (2.0 * js2 + 3.0 * n2) * fb);
-            if ((rc = launch_multidot(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk,
+            ProfScope ps(&ctx->prof, "cgs_reorth", (2.0 * js2 + 3.0 * n2) * fv);
+            if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk,
                                       dots, st)))
                 return rc;
-            if ((rc = launch_multiaxpy(op, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial,
+            if ((rc = launch_multiaxpy(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial,
                                        nblk, norm2d, st)))
                 return rc;
         }
@@ -492,8 +544,8 @@ int Solver::step() {
     DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
     DW_CUDA_TRY(cudaMemcpyAsync(norm2d, norm2_h, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
-        ProfScope ps(&ctx->prof, "normalize", (double)nact * (2.0 * fb + sb));
-        if ((rc = launch_normalize(op, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, sp, Lf, st)))
+        ProfScope ps(&ctx->prof, "normalize", (double)nact * (2.0 * fv + sb));
+        if ((rc = launch_normalize(vp, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, sp, Lf, st)))
             return rc;
     }
     // host: Hessenberg column, Givens update, end-of-cycle tests

@@ -135,14 +135,25 @@ def test_dense_solve(dw):
     assert np.linalg.norm(A @ x - b) < 1e-12 * np.linalg.norm(b)
 
 
-def test_request_bytes_formula(dw):
-    """Admission estimate: gauge copies + staging + per-rhs Krylov workspace."""
-    P = dw.dw_default_params(m=30, k=10, nrhs=3, sap_prec=dw.DW_F16)
+@pytest.mark.parametrize("k,outer", [(10, None), (0, None), (10, "f32")])
+def test_request_bytes_formula(dw, k, outer):
+    """Admission estimate: gauge copies (FP64, staging, FP32, FP16, double-float)
+    + per-rhs Krylov workspace (V in the basis format; Z in FP32 when a 16-bit
+    SAP is deflated, with the SAP output buffer; x, b, r; SAP input copy;
+    canonical staging) + rotation scratch."""
+    kw = dict(m=30, k=k, nrhs=3, sap_prec=dw.DW_F16)
+    if outer == "f32":
+        kw["outer_prec"] = dw.DW_F32
+    P = dw.dw_default_params(**kw)
     dims = (16, 16, 16, 32)
     V = 16 * 16 * 16 * 32
     req = dw.make_request(dims, (4, 4, 4, 4), -0.6, 1, 1, 1, P)
     sb = 52 * V
-    gauge = 576 * V + 576 * V + 288 * V + 144 * V
-    per_rhs = 31 * 192 * V + 30 * sb + 3 * 192 * V + sb + 24 * 8 * V
-    expect = gauge + 3 * per_rhs + 10 * sb + (8 << 20)
+    zb = 96 * V if k > 0 else sb
+    fv = 96 * V if outer == "f32" else 192 * V
+    gauge = 576 * V + 576 * V + 288 * V + 144 * V + 576 * V
+    per_rhs = 31 * fv + 30 * zb + 3 * 192 * V + sb + 24 * 8 * V
+    per_rhs += sb if zb != sb else 0
+    per_rhs += fv if outer == "f32" else 0
+    expect = gauge + 3 * per_rhs + max(k, 1) * zb + (8 << 20)
     assert dw.dw_request_bytes(req) == expect

@@ -185,15 +185,49 @@ def test_fgmresdr_low_precision_sap_converges(dw, sap_prec):
         assert abs(S.iterations - ref.iterations) <= max(3, 0.15 * ref.iterations)
 
 
+@pytest.mark.parametrize("sap_prec", [1, 2])
+def test_fgmresdr_fp32_basis_converges(dw, sap_prec):
+    """Single-precision Arnoldi process with double-float refinement (Sec. 4.7):
+    the FP32 basis still reaches the 1e-10 true residual (checked with the
+    oracle's D), within cond*tol of the oracle solution, in a comparable number
+    of Arnoldi steps."""
+    cfg, U, b = _tiny()
+    ref = oracle.solve(U, b, cfg["dims"], cfg["block"], cfg["m0"], cfg["sap_cycles"], cfg["mr_steps"], cfg["m"],
+                       cfg["k"], cfg["tol"])
+    x, S = _solve(dw, cfg, U, b, sap_prec=sap_prec, matvec_prec=1, outer_prec=1)
+    assert S.converged == 1
+    r = b - oracle.dw(U, x, cfg["dims"], cfg["m0"])
+    assert np.linalg.norm(r) <= cfg["tol"] * np.linalg.norm(b)
+    assert rel2(x.reshape(-1), ref.x) <= 100 * cfg["tol"]
+    assert S.iterations <= 1.5 * ref.iterations + 5
+
+
+def test_fgmresdr_fp32_basis_larger_lattice(dw):
+    """8^3 x 16 near criticality: the FP32 basis converges to the true residual
+    with at most 30% more Arnoldi steps than the double-float basis."""
+    dims, block = (8, 8, 8, 16), (4, 4, 4, 4)
+    U = fg.gauge_field(dims, 0.45, seed=0)
+    b = fg.gaussian_source(dims, 3)
+    m0 = fg.tuned_m0(dims, 0.45, 0, 1e-2)  # smallest |eigenvalue| about 1e-2: a slow solve
+    cfg = {"dims": dims, "block": block, "m0": m0, "m": 30, "k": 10, "tol": 1e-10, "sap_cycles": 5, "mr_steps": 4}
+    x64, S64 = _solve(dw, cfg, U, b, sap_prec=1, matvec_prec=1, outer_prec=4)
+    x32, S32 = _solve(dw, cfg, U, b, sap_prec=1, matvec_prec=1, outer_prec=1)
+    assert S64.converged == 1 and S32.converged == 1
+    r = b - oracle.dw(U, x32, dims, m0)
+    assert np.linalg.norm(r) <= cfg["tol"] * np.linalg.norm(b)
+    assert S32.iterations <= 1.3 * S64.iterations + 5
+
+
 @pytest.mark.parametrize("k", [0, 3])
-@pytest.mark.parametrize("outer", [0, 4])
+@pytest.mark.parametrize("outer", [0, 4, 1])
 def test_fgmresdr_batched_equals_single(dw, k, outer):
     cfg, U, _ = _tiny()
     bs = fg.gaussian_source(cfg["dims"], 7, nrhs=3)
-    xb, Sb = _solve(dw, cfg, U, bs, nrhs=3, k=k, outer_prec=outer)
+    kw = dict(k=k, outer_prec=outer) if outer != 1 else dict(k=k, outer_prec=outer, sap_prec=1, matvec_prec=1)
+    xb, Sb = _solve(dw, cfg, U, bs, nrhs=3, **kw)
     assert Sb.converged == 3
     for r in range(3):
-        x1, S1 = _solve(dw, cfg, U, bs[r], k=k, outer_prec=outer)
+        x1, S1 = _solve(dw, cfg, U, bs[r], **kw)
         assert S1.iterations == Sb.iterations_rhs[r]
         assert rel2(xb[r].reshape(-1), x1.reshape(-1)) <= 1e-12
 
