@@ -116,9 +116,10 @@ def kernel_traffic(name):
     e = t.get(name)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_1204_5463_gb300", "csrc", e["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != e.get("source_sha256_16"):
+    m = hashlib.sha256()
+    for src in e["sources"]:
+        m.update(open(os.path.join(ROOT, "paper_1204_5463_gb300", "csrc", src), "rb").read())
+    if m.hexdigest()[:16] != e.get("source_sha256_16"):
         return None
     return e["bytes_per_launch"] * e.get("scale", 1.0)
 
@@ -165,7 +166,8 @@ def dw_bandwidth(peaks, reps=10):
         avg_s = d["total_ms"] / d["launches"] / 1e3
         gbs = d["bytes"] / d["launches"] / avg_s / 1e9
         out[name] = {"GB/s": gbs, "frac": gbs / peaks["hbm_gbs"], "avg_us": avg_s * 1e6,
-                     "bytes_per_site": d["bytes"] / d["launches"] / fg.volume(dims)}
+                     "bytes_per_site": d["bytes"] / d["launches"] / fg.volume(dims),
+                     "traffic": kernel_traffic("dw_" + name)}
     dw.dw_destroy(ctx)
     return out
 
