@@ -11,6 +11,9 @@
 //         would otherwise cap these HBM-bound sweeps far below bandwidth.
 // Reductions are deterministic: every CTA writes its partial sums (FP64) to a
 // fixed slot and one CTA per right-hand side adds the slots in order.
+#include <mutex>
+#include <set>
+
 #include "internal.h"
 
 namespace dwk {
@@ -177,12 +180,20 @@ struct Elem<PDF> {
 
 // ---- multi-dot: partial[r][blk][i] = <V_i, w> (i < nv), [nvmax] = ||w||^2 ---
 // The CTAs of one group of 8 basis vectors split the elements between them
-// (grid stride); each thread reads w[e] once into registers and the 8 V_i[e]
-// of its group, so every V_i element is read once, coalesced, with the loads
-// of two elements (16 words) in flight per thread and no shared-memory
-// staging or barriers in the stream. The warp reductions happen once per CTA
-// at the end.
-constexpr int kDotG = 8;  // basis vectors per CTA
+// (grid stride). Each thread streams its elements of w and of the 8 V_i
+// through a private ring of kDotStages shared-memory slots with cp.async, so
+// the loads of the next kDotStages - 1 elements are in flight while the
+// current one is multiplied: the memory pipeline stays full without holding
+// the in-flight data in registers. A thread reads back only the slots it
+// filled itself, so no barrier is needed. Every V_i element is read once,
+// coalesced; the warp reductions happen once per CTA at the end.
+constexpr int kDotG = 8;       // basis vectors per CTA
+constexpr int kDotStages = 3;  // elements in flight per thread
+
+template <int VP>
+constexpr size_t multidot_smem() {
+    return (size_t)kDotStages * (kDotG + 1) * kT * sizeof(typename Elem<VP>::T);
+}
 
 // partial[r][slot][i] over the elements this CTA sweeps, for its group of 8
 // vectors; the CTAs of group 0 also write ||w||^2 and zero the unused slots.
@@ -191,6 +202,9 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
                                                          int nv_off, int nvmax, int ngroups, double2* partial) {
     typedef Elem<VP> E;
     typedef typename E::C C;
+    typedef typename E::T TW;  // storage word of one complex element
+    extern __shared__ __align__(16) unsigned char dsm[];
+    TW* ring = reinterpret_cast<TW*>(dsm);  // [kDotStages][kDotG + 1][kT]
     __shared__ double2 red[kDotG][kT / 32];
     __shared__ double redn[kT / 32];
     const int r = blockIdx.y;
@@ -203,27 +217,46 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int i0 = grp * kDotG;
     const int G = max(0, min(kDotG, nv - i0));  // vectors of this CTA
-    const double2* Vr = Vb.base + r * Vb.rhs_stride + (long long)(Vb.col_off + i0) * Vb.col_stride;
-    const double2* wr = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
+    const TW* Vr = reinterpret_cast<const TW*>(Vb.base + r * Vb.rhs_stride +
+                                               (long long)(Vb.col_off + i0) * Vb.col_stride);
+    const long long cs = Vb.col_stride * (long long)(16 / sizeof(TW));  // column stride in words
+    const TW* wr = reinterpret_cast<const TW*>(w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride);
     C acc[kDotG];
 #pragma unroll
     for (int q = 0; q < kDotG; ++q) acc[q] = E::zero();
     typename E::N wacc = E::nzero();
     const long long stride = (long long)nslots * kT;
-    // element-outer, vector-inner: the G accumulators are independent
-    // dependency chains, and the G loads of one element are in flight together
-#pragma unroll 2
-    for (long long e = (long long)slot * kT + t; e < n; e += stride) {
-        const C wv = E::load(wr, e);
-        if (grp == 0) E::norm2_acc(wacc, wv);
-        C vv[kDotG];
+    auto issue = [&](long long e, int stage) {
+        if (e < n) {
+            TW* sl = ring + (size_t)stage * (kDotG + 1) * kT + t;
+            cp_async_word(sl + kDotG * kT, wr + e);
 #pragma unroll
-        for (int q = 0; q < kDotG; ++q)
-            if (q < G) vv[q] = E::load(Vr + (long long)q * Vb.col_stride, e);
+            for (int q = 0; q < kDotG; ++q)
+                if (q < G) cp_async_word(sl + q * kT, Vr + q * cs + e);
+        }
+        cp_async_commit();  // one group per element slot, empty past the end
+    };
+    long long e_next = (long long)slot * kT + t;
 #pragma unroll
-        for (int q = 0; q < kDotG; ++q)
-            if (q < G) E::mac_conj(acc[q], vv[q], wv);
+    for (int sg = 0; sg < kDotStages - 1; ++sg) {
+        issue(e_next, sg);
+        e_next += stride;
     }
+    int sc = 0, si = kDotStages - 1;
+    for (long long e = (long long)slot * kT + t; e < n; e += stride) {
+        issue(e_next, si);
+        e_next += stride;
+        si = (si + 1 == kDotStages) ? 0 : si + 1;
+        cp_async_wait_pending<kDotStages - 1>();  // the slot of element e has landed
+        const TW* sl = ring + (size_t)sc * (kDotG + 1) * kT + t;
+        const C wv = E::load_rw(reinterpret_cast<const double2*>(sl + kDotG * kT), 0);
+        if (grp == 0) E::norm2_acc(wacc, wv);
+#pragma unroll
+        for (int q = 0; q < kDotG; ++q)
+            if (q < G) E::mac_conj(acc[q], E::load_rw(reinterpret_cast<const double2*>(sl + q * kT), 0), wv);
+        sc = (sc + 1 == kDotStages) ? 0 : sc + 1;
+    }
+    cp_async_wait_pending<0>();
     // CTA reduction of the G dot products (warp shuffles, then across warps)
 #pragma unroll
     for (int q = 0; q < kDotG; ++q)
@@ -559,24 +592,42 @@ bool basis_ok(int vp) { return vp == P64 || vp == PDF || vp == P32; }
 
 int blas_nblk(long long n) { return (int)grid_for(n); }
 
-int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
-                    double2* partial, int nblk, double2* out, cudaStream_t st) {
+int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nv_active,
+                    int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
     if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
     // CTAs: (element slots) x (groups of 8 vectors), one wave of two CTAs per
     // SM per right-hand side; at most nblk slots
-    const int ngroups = (nvmax + kDotG - 1) / kDotG;
+    if (nv_active < 1 || nv_active > nvmax) nv_active = nvmax;
+    const int ngroups = (nv_active + kDotG - 1) / kDotG;  // groups past every rhs's nv would only read w
     long long nb = (152LL * 2 + ngroups - 1) / ngroups;
     if (nb > nblk) nb = nblk;
     if (nb > (n + kT - 1) / kT) nb = (n + kT - 1) / kT;
     if (nb < 1) nb = 1;
     const dim3 grid((unsigned)(nb * ngroups), nrhs);
+    // the ring exceeds the 48 KB default: raise the limit once per device
+    static std::mutex mu;
+    static std::set<int> done;
+    {
+        int dev = 0;
+        DW_CUDA_TRY(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done.count(dev)) {
+            DW_CUDA_TRY(cudaFuncSetAttribute(multidot_kernel<PDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)multidot_smem<PDF>()));
+            DW_CUDA_TRY(cudaFuncSetAttribute(multidot_kernel<P64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)multidot_smem<P64>()));
+            DW_CUDA_TRY(cudaFuncSetAttribute(multidot_kernel<P32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)multidot_smem<P32>()));
+            done.insert(dev);
+        }
+    }
     if (vp == PDF)
-        multidot_kernel<PDF><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+        multidot_kernel<PDF><<<grid, kT, multidot_smem<PDF>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     else if (vp == P32)
-        multidot_kernel<P32><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+        multidot_kernel<P32><<<grid, kT, multidot_smem<P32>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     else
-        multidot_kernel<P64><<<grid, kT, 0, st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+        multidot_kernel<P64><<<grid, kT, multidot_smem<P64>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
     DW_LAUNCH_CHECK();
     finalize_kernel<<<nrhs, 1024, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
     DW_LAUNCH_CHECK();

@@ -185,6 +185,27 @@ __device__ __forceinline__ df operator-(df a, df b) { return df_add(a, df_neg(b)
 __device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
 
 #ifdef __CUDACC__
+// asynchronous global -> shared copy of one 4/8/16-byte word (cp.async)
+template <class W>
+__device__ __forceinline__ void cp_async_word(W* smem_dst, const W* gsrc) {
+    static_assert(sizeof(W) == 4 || sizeof(W) == 8 || sizeof(W) == 16, "cp.async word size");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(W) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(sizeof(W)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+    cp_async_commit();
+    cp_async_wait_pending<0>();
+}
+
 // warp-wide sum of a double-float value (every lane gets the sum)
 __device__ __forceinline__ df df_warp_sum(df a) {
 #pragma unroll

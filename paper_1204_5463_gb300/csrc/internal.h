@@ -136,8 +136,10 @@ struct VecRef {
     int col_off;
 };
 // out[r][i] = <V_i, w>  (i < nv[r]),  out[r][nvmax] = ||w||^2 ; nv = jtab[r] + nv_off (or nv_off)
-int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nrhs,
-                    double2* partial, int nblk, double2* out, cudaStream_t st);
+// nv_active: the largest number of basis vectors any rhs has in this launch
+// (sizes the grid); nvmax: the row length of partial/out minus one
+int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nv_active,
+                    int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st);
 // w -= sum_i coef[r][i] V_i (i < nv[r]);  out_norm2[r] = ||w||^2 after the update
 int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs,
                      const double2* coef, int coef_ld, double2* partial, int nblk, double* out_norm2,

@@ -22,20 +22,6 @@ namespace dwk {
 
 namespace {
 
-// asynchronous global -> shared copy of one 4/8/16-byte word
-template <class W>
-__device__ __forceinline__ void cp_async_word(W* smem_dst, const W* gsrc) {
-    static_assert(sizeof(W) == 4 || sizeof(W) == 8 || sizeof(W) == 16, "cp.async word size");
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if constexpr (sizeof(W) == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(sizeof(W)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 // The domain's own links in shared memory, packed so that one link matrix
 // (9 complex entries) is read with as few wide loads as possible:
 //   P64      double2 [4][9][T]                                          (9 x 16 B loads)

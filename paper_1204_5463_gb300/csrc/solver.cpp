@@ -78,6 +78,8 @@ struct Solver {
     double2* dots_h;
     double* norm2_h;
     int* jtab_h;
+    double* norm2_up;  // upload copies for the end of a step (the next step rewrites jtab_h
+    int* jtab_up;      // before the device has necessarily consumed the previous upload)
     std::vector<RhsState> R;
     int explicit_res = 0;
 
@@ -137,11 +139,15 @@ struct Workspace {
     double2* dots_h = nullptr;
     double* norm2_h = nullptr;
     int* jtab_h = nullptr;
+    double* norm2_up = nullptr;
+    int* jtab_up = nullptr;
     size_t dots_h_n = 0;
     ~Workspace() {
         if (dots_h) cudaFreeHost(dots_h);
         if (norm2_h) cudaFreeHost(norm2_h);
         if (jtab_h) cudaFreeHost(jtab_h);
+        if (norm2_up) cudaFreeHost(norm2_up);
+        if (jtab_up) cudaFreeHost(jtab_up);
     }
 };
 
@@ -207,12 +213,18 @@ int Solver::setup() {
         if (W->dots_h) cudaFreeHost(W->dots_h);
         if (W->norm2_h) cudaFreeHost(W->norm2_h);
         if (W->jtab_h) cudaFreeHost(W->jtab_h);
+        if (W->norm2_up) cudaFreeHost(W->norm2_up);
+        if (W->jtab_up) cudaFreeHost(W->jtab_up);
+        W->norm2_up = nullptr;
+        W->jtab_up = nullptr;
         W->dots_h = nullptr;
         W->norm2_h = nullptr;
         W->jtab_h = nullptr;
         DW_CUDA_TRY(cudaMallocHost(&W->dots_h, (size_t)2 * DW_MAX_RHS * 66 * sizeof(double2)));
         DW_CUDA_TRY(cudaMallocHost(&W->norm2_h, (size_t)DW_MAX_RHS * sizeof(double)));
         DW_CUDA_TRY(cudaMallocHost(&W->jtab_h, (size_t)DW_MAX_RHS * sizeof(int)));
+        DW_CUDA_TRY(cudaMallocHost(&W->norm2_up, (size_t)DW_MAX_RHS * sizeof(double)));
+        DW_CUDA_TRY(cudaMallocHost(&W->jtab_up, (size_t)DW_MAX_RHS * sizeof(int)));
         W->dots_h_n = (size_t)DW_MAX_RHS * 66;
     }
     Vb = W->V.as<char>();
@@ -235,6 +247,8 @@ int Solver::setup() {
     dots_h = W->dots_h;
     norm2_h = W->norm2_h;
     jtab_h = W->jtab_h;
+    norm2_up = W->norm2_up;
+    jtab_up = W->jtab_up;
     R.assign(nrhs, RhsState());
     for (auto& s : R) {
         s.H.assign((size_t)(m + 1) * m, zd(0));
@@ -294,8 +308,8 @@ int Solver::start_deflated(int r) {
     if ((rc = residual_to_basis(r))) return rc;
     {
         ProfScope ps(&ctx->prof, "multidot", (double)(mm + 2) * fv);
-        if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, mm + 1, m + 1, 1, partial, nblk, dots,
-                                  st)))
+        if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, mm + 1, m + 1, mm + 1, 1, partial,
+                                  nblk, dots, st)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * NP, cudaMemcpyDeviceToHost, st));
@@ -346,7 +360,7 @@ int Solver::start_deflated(int r) {
     for (int pass = 0; pass < 2; ++pass) {
         ProfScope ps(&ctx->prof, "cgs", (double)(2 * k + 3) * fv);
         VecRef w = vref_all(r, k);
-        if ((rc = launch_multidot(vp, vref_all(r, 0), w, n, nullptr, k, m + 1, 1, partial, nblk, dots, st)))
+        if ((rc = launch_multidot(vp, vref_all(r, 0), w, n, nullptr, k, m + 1, k, 1, partial, nblk, dots, st)))
             return rc;
         if ((rc = launch_multiaxpy(vp, vref_all(r, 0), w, n, nullptr, k, 1, dots, NP, partial, nblk, norm2d + r,
                                    st)))
@@ -361,7 +375,7 @@ int Solver::start_deflated(int r) {
     // c = [V_{k+1}^H r; 0]
     {
         ProfScope ps(&ctx->prof, "multidot", (double)(k1 + 1) * fv);
-        if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, k1, m + 1, 1, partial, nblk, dots,
+        if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, k1, m + 1, k1, 1, partial, nblk, dots,
                                   st)))
             return rc;
     }
@@ -477,12 +491,13 @@ int Solver::step() {
     // ("twice is enough") only where cancellation could cost orthogonality at
     // the working precision: u / (||w'|| / ||w||) > 1e-13
     double jsum = 0;
+    int jmax = 0;
     for (int r = 0; r < nrhs; ++r)
-        if (jtab_h[r] >= 0) jsum += jtab_h[r] + 1;
+        if (jtab_h[r] >= 0) jsum += jtab_h[r] + 1, jmax = std::max(jmax, jtab_h[r]);
     {
         ProfScope ps(&ctx->prof, "cgs_project", (jsum + nact) * fv);
-        if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk, dots,
-                                  st)))
+        if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, jmax + 1, nrhs, partial,
+                                  nblk, dots, st)))
             return rc;
     }
     {
@@ -515,14 +530,14 @@ int Solver::step() {
     if (need2) {
         DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
         double js2 = 0;
-        int n2 = 0;
+        int n2 = 0, jmax2 = 0;
         for (int r = 0; r < nrhs; ++r)
-            if (jtab_h[r] >= 0) js2 += jtab_h[r] + 1, ++n2;
+            if (jtab_h[r] >= 0) js2 += jtab_h[r] + 1, ++n2, jmax2 = std::max(jmax2, jtab_h[r]);
         std::vector<double> keep(norm2_h, norm2_h + nrhs);
         {
             ProfScope ps(&ctx->prof, "cgs_reorth", (2.0 * js2 + 3.0 * n2) * fv);
-            if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, nrhs, partial, nblk,
-                                      dots, st)))
+            if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, jmax2 + 1, nrhs,
+                                      partial, nblk, dots, st)))
                 return rc;
             if ((rc = launch_multiaxpy(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial,
                                        nblk, norm2d, st)))
@@ -540,9 +555,13 @@ int Solver::step() {
         }
     }
     // restore the step's column table; v_{j+1} = w / ||w|| (also into SAP storage)
-    for (int r = 0; r < nrhs; ++r) jtab_h[r] = (!R[r].done && R[r].j >= 0) ? R[r].j : -1;
-    DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-    DW_CUDA_TRY(cudaMemcpyAsync(norm2d, norm2_h, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    for (int r = 0; r < nrhs; ++r) {
+        jtab_h[r] = (!R[r].done && R[r].j >= 0) ? R[r].j : -1;
+        jtab_up[r] = jtab_h[r];
+        norm2_up[r] = norm2_h[r];
+    }
+    DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_up, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    DW_CUDA_TRY(cudaMemcpyAsync(norm2d, norm2_up, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     {
         ProfScope ps(&ctx->prof, "normalize", (double)nact * (2.0 * fv + sb));
         if ((rc = launch_normalize(vp, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, sp, Lf, st)))
@@ -579,7 +598,9 @@ int Solver::step() {
             s.j = j + 1;
         }
     }
-    if ((rc = sync())) return rc;
+    // no synchronisation here: the next step's launches queue behind the
+    // normalisation (its uploads read jtab_up / norm2_up, which are only
+    // rewritten after the next step's first synchronisation)
     for (int r = 0; r < nrhs; ++r)
         if (R[r].cycle_end) {
             R[r].cycle_end = false;
