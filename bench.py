@@ -479,11 +479,10 @@ def main():
         torch.cuda.synchronize()
 
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    dw.dw_profile(ctx, True)
-    dw.dw_profile_read(ctx, reset=True)
     barrier()
     if clocks:
         clocks.start()
+    # timed region 1: K solves as a user runs them (no per-kernel events)
     launches0 = dw.dw_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -501,14 +500,29 @@ def main():
     ev1.record(stream)
     barrier()
     launches = dw.dw_kernel_launches() - launches0
+    # timed region 2: the same K solves with the library's per-kernel CUDA
+    # events on the solver's stream (the roofline and the kernel shares); the
+    # events themselves cost wall time, so the headline comes from region 1
+    dw.dw_profile(ctx, True)
+    dw.dw_profile_read(ctx, reset=True)
+    barrier()
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(args.steps):
+        S = dw.fgmresdr_solve(ctx, bd, xd, P)
+        assert S.converged == 1 and S.true_rel_res[0] <= cfg["tol"]
+    pe1.record(stream)
+    barrier()
     clk = clocks.stop() if clocks else None
     prof = dw.dw_profile_read(ctx, reset=True)
     dw.dw_profile(ctx, False)
+    ms_prof = pe0.elapsed_time(pe1)
     ms = ev0.elapsed_time(ev1)
     if dist:
-        t = torch.tensor([ms], device="cuda")
+        t = torch.tensor([ms, ms_prof], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, ms_prof = float(t[0].item()), float(t[1].item())
     value = args.steps * world / (ms / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the call
@@ -621,6 +635,9 @@ def main():
         "roofline": roof,
         "kernel_share": shares,
         "kernel_avg_us": avg_us,
+        "profiled_pass": {"ms_per_step": ms_prof / args.steps, "steps": args.steps,
+                          "note": "second timed pass with per-kernel CUDA events (roofline, kernel_share, "
+                                  "kernel_avg_us); value is the pass without them"},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(bh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8)},
         "gpu_launches": int(launches),
