@@ -217,11 +217,21 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     const long long s = site_index(g, xg);
     const int ls1 = g.b[0], ls2 = g.b[0] * g.b[1], ls3 = g.b[0] * g.b[1] * g.b[2];  // in-domain strides
 
+    // 0. programmatic dependent launch: the next sweep may be scheduled onto
+    //    SMs as this one's CTAs retire, and stage its links meanwhile
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     // 1. asynchronous copies global -> shared, all in flight together: the
-    //    domain's own links and, in the general mode, its own iterate x in
-    //    storage layout (stride T), read by interior hops
+    //    domain's own links (constant during a solve, so copied before the
+    //    previous sweep has finished) and, once that sweep's x is final, in
+    //    the general mode the domain's own iterate x in storage layout
+    //    (stride T), read by interior hops
+    if (act) LS::stage(lsh, T, tid, U, g.V, s);
+    // every read of v and x and every write of x comes after the previous
+    // kernel of the stream has completed (a no-op without a programmatic
+    // dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (act) {
-        LS::stage(lsh, T, tid, U, g.V, s);
         if (mode == 2) {
             if constexpr (PS == P64) {
                 for (int c = 0; c < 12; ++c)
@@ -392,12 +402,27 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
         }
     }
     const unsigned nb = (unsigned)(g.ndom / 2) * (unsigned)nrhs;
+    // launched with programmatic stream serialisation: when the previous
+    // kernel of the stream is a sweep, this one starts staging its links
+    // during that sweep's tail (the kernel waits for the previous grid before
+    // it touches v or x)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const C diag = (C)(4.0 + m0);
     if (threads <= 256)
-        sap_sweep_kernel<PS, PL, C, 256><<<nb, threads, smem, st>>>(g, (C)(4.0 + m0), v, x, U, jtab, nrhs, colour,
-                                                                     nmr, mode);
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256>, g, diag, v, x, U, jtab, nrhs, colour,
+                                       nmr, mode));
     else
-        sap_sweep_kernel<PS, PL, C, 1024><<<nb, threads, smem, st>>>(g, (C)(4.0 + m0), v, x, U, jtab, nrhs, colour,
-                                                                      nmr, mode);
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024>, g, diag, v, x, U, jtab, nrhs, colour,
+                                       nmr, mode));
     DW_LAUNCH_CHECK();
     return DW_OK;
 }
