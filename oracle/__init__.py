@@ -12,6 +12,9 @@ Flexible SAP-Preconditioning of GMRES in Lattice QCD Simulation"):
   (``dw_oracle.c``), mass form ``D = (4+m0) - 1/2 H_hop = D_kappa/(2 kappa)``.
 * ``sap`` -- Algorithm 2 (SAP iteration) with minimal-residual local solves
   (Sec. 3), in C.
+* ``clover`` -- the site-diagonal clover term of the improved operators of
+  Sec. 5 (a reading: the paper cites it without a formula), in C; ``dw``,
+  ``dw_local`` and ``sap`` add it when given.
 * ``flexible_arnoldi`` -- Algorithm 3 (flexible Arnoldi, modified Gram-Schmidt
   as printed).
 * ``fgmresdr`` -- Algorithm 4 (F-GMRES-DR) with the harmonic Ritz extraction of
@@ -67,6 +70,14 @@ def _lib():
         lib.oracle_site_colours.restype = None
         lib.oracle_mr_history.argtypes = [P, P, ctypes.c_double, P, P, P, ctypes.c_int, ctypes.c_int, P]
         lib.oracle_mr_history.restype = ctypes.c_int
+        lib.oracle_dw_c.argtypes = [P, ctypes.c_double, P, P, P, P]
+        lib.oracle_dw_c.restype = None
+        lib.oracle_dw_local_c.argtypes = [P, P, ctypes.c_double, P, P, P, P, ctypes.c_int]
+        lib.oracle_dw_local_c.restype = None
+        lib.oracle_sap_c.argtypes = [P, P, ctypes.c_double, P, P, P, P, ctypes.c_int, ctypes.c_int]
+        lib.oracle_sap_c.restype = ctypes.c_int
+        lib.oracle_clover.argtypes = [P, ctypes.c_double, P, P]
+        lib.oracle_clover.restype = None
         _lib_handle = lib
     return _lib_handle
 
@@ -93,33 +104,59 @@ def gamma(mu: int) -> np.ndarray:
     return out
 
 
-def dw(U, psi, dims, m0: float) -> np.ndarray:
-    """D psi on the full periodic lattice (Eq. "Dw"); psi shape (V,4,3) or flat."""
+def clover(U, dims, csw: float) -> np.ndarray:
+    """The clover term A[site] (12 x 12 complex, index 3*spin + colour) with
+    coefficient csw: c_sw (i/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu} from the
+    clover-leaf field strength (the reading stated in dw_oracle.c)."""
+    U = _cvec(U)
+    V = int(np.prod(dims))
+    A = np.empty((V, 12, 12), dtype=np.complex128)
+    _lib().oracle_clover(_ptr(_ivec(dims)), float(csw), _ptr(U), _ptr(A))
+    return A
+
+
+def dw(U, psi, dims, m0: float, A=None) -> np.ndarray:
+    """D psi on the full periodic lattice (Eq. "Dw"), plus the clover term A psi
+    when A is given; psi shape (V,4,3) or flat."""
     U = _cvec(U)
     psi = _cvec(psi)
     out = np.empty_like(psi)
     d = _ivec(dims)
-    _lib().oracle_dw(_ptr(d), float(m0), _ptr(U), _ptr(psi), _ptr(out))
+    if A is None:
+        _lib().oracle_dw(_ptr(d), float(m0), _ptr(U), _ptr(psi), _ptr(out))
+    else:
+        A = _cvec(A)
+        _lib().oracle_dw_c(_ptr(d), float(m0), _ptr(U), _ptr(A), _ptr(psi), _ptr(out))
     return out
 
 
-def dw_local(U, psi, dims, block, m0: float, colour: int = -1) -> np.ndarray:
+def dw_local(U, psi, dims, block, m0: float, colour: int = -1, A=None) -> np.ndarray:
     """Block-diagonal D^l psi on all domains (colour=-1) or the domains of one colour."""
     U = _cvec(U)
     psi = _cvec(psi)
     out = np.empty_like(psi)
-    _lib().oracle_dw_local(_ptr(_ivec(dims)), _ptr(_ivec(block)), float(m0), _ptr(U), _ptr(psi), _ptr(out),
-                           int(colour))
+    if A is None:
+        _lib().oracle_dw_local(_ptr(_ivec(dims)), _ptr(_ivec(block)), float(m0), _ptr(U), _ptr(psi), _ptr(out),
+                               int(colour))
+    else:
+        A = _cvec(A)
+        _lib().oracle_dw_local_c(_ptr(_ivec(dims)), _ptr(_ivec(block)), float(m0), _ptr(U), _ptr(A), _ptr(psi),
+                                 _ptr(out), int(colour))
     return out
 
 
-def sap(U, b, dims, block, m0: float, ncycles: int, nmr: int, x0=None) -> np.ndarray:
+def sap(U, b, dims, block, m0: float, ncycles: int, nmr: int, x0=None, A=None) -> np.ndarray:
     """``ncycles`` SAP iterations (Algorithm 2) from x0 (default 0); nmr=0: exact local solves."""
     U = _cvec(U)
     b = _cvec(b)
     x = np.zeros_like(b) if x0 is None else _cvec(x0).copy()
-    rc = _lib().oracle_sap(_ptr(_ivec(dims)), _ptr(_ivec(block)), float(m0), _ptr(U), _ptr(b), _ptr(x),
-                           int(ncycles), int(nmr))
+    if A is None:
+        rc = _lib().oracle_sap(_ptr(_ivec(dims)), _ptr(_ivec(block)), float(m0), _ptr(U), _ptr(b), _ptr(x),
+                               int(ncycles), int(nmr))
+    else:
+        A = _cvec(A)
+        rc = _lib().oracle_sap_c(_ptr(_ivec(dims)), _ptr(_ivec(block)), float(m0), _ptr(U), _ptr(A), _ptr(b),
+                                 _ptr(x), int(ncycles), int(nmr))
     if rc != 0:
         raise RuntimeError(f"oracle_sap failed ({rc})")
     return x
@@ -367,22 +404,23 @@ def fgmresdr(A, M, b, m: int, k: int, tol: float, max_cycles: int = 1000, t_clea
 # Lattice-level conveniences
 # ----------------------------------------------------------------------------
 
-def lattice_operators(U, dims, block, m0, sap_cycles: int, mr_steps: int):
-    """(A, M) callables on flat complex vectors: A = D, M = SAP preconditioner."""
+def lattice_operators(U, dims, block, m0, sap_cycles: int, mr_steps: int, clov=None):
+    """(A, M) callables on flat complex vectors: A = D (plus the clover term
+    clov when given), M = SAP preconditioner built on the same operator."""
     U = _cvec(U)
     V = int(np.prod(dims))
 
     def A(v):
-        return dw(U, np.asarray(v).reshape(V, 4, 3), dims, m0).reshape(-1)
+        return dw(U, np.asarray(v).reshape(V, 4, 3), dims, m0, A=clov).reshape(-1)
 
     def M(v):
-        return sap(U, np.asarray(v).reshape(V, 4, 3), dims, block, m0, sap_cycles, mr_steps).reshape(-1)
+        return sap(U, np.asarray(v).reshape(V, 4, 3), dims, block, m0, sap_cycles, mr_steps, A=clov).reshape(-1)
 
     return A, M
 
 
-def solve(U, b, dims, block, m0, sap_cycles, mr_steps, m, k, tol, **kw) -> SolveResult:
-    A, M = lattice_operators(U, dims, block, m0, sap_cycles, mr_steps)
+def solve(U, b, dims, block, m0, sap_cycles, mr_steps, m, k, tol, clov=None, **kw) -> SolveResult:
+    A, M = lattice_operators(U, dims, block, m0, sap_cycles, mr_steps, clov=clov)
     return fgmresdr(A, M, np.asarray(b).reshape(-1), m, k, tol, **kw)
 
 

@@ -26,6 +26,15 @@
  * Each sweep computes r^l = (b - D x)^l with the full operator, approximately
  * solves D^l y^l = r^l, and adds the correction: x^l <- x^l + y^l.
  *
+ * Clover term (the Sheikholeslami-Wohlert improvement of the operators in
+ * Sec. 5; the paper cites it without a formula, so this is a reading): a
+ * site-diagonal 12x12 matrix added to D and to every D^l,
+ *   A_n = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(n),
+ *   sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu],
+ *   F_{mu nu}(n) = (1/8) (Q - Q^dagger) minus its trace / 3,
+ * with Q the sum of the four plaquettes in the (mu, nu) plane that start and
+ * end at n, all traversed in the same sense (mu first, then nu).
+ *
  * Local solver (Sec. 3): nmr steps of minimal residual (MR) from y = 0:
  *   p = D^l rho;  alpha = <p,rho>/<p,p>  (<a,b> = a^H b);  y += alpha rho;
  *   rho -= alpha p.  nmr == 0 selects an exact solve by Gaussian elimination
@@ -112,10 +121,13 @@ static int colour_of_domain(const lattice *L, long dom) {
 
 /* One site of D (all hops) or of the block-diagonal local operator (only hops
  * inside the domain of site s). in/out point at 12-complex spinors.           */
-static void apply_site(const lattice *L, double m0, const cplx *U, const cplx *in, long s, int local,
-                       cplx out[12]) {
+static void apply_site(const lattice *L, double m0, const cplx *U, const cplx *A, const cplx *in, long s,
+                       int local, cplx out[12]) {
     const long dom = local ? domain_of(L, s) : -1;
     for (int a = 0; a < 12; ++a) out[a] = (4.0 + m0) * in[12 * s + a];
+    if (A) /* clover term: site-diagonal, part of D and of every D^l */
+        for (int a = 0; a < 12; ++a)
+            for (int b = 0; b < 12; ++b) out[a] += A[144 * s + 12 * a + b] * in[12 * s + b];
     for (int mu = 0; mu < 4; ++mu) {
         for (int sign = +1; sign >= -1; sign -= 2) {
             const long t = hop(L, s, mu, sign);
@@ -144,23 +156,29 @@ static void apply_site(const lattice *L, double m0, const cplx *U, const cplx *i
 }
 
 /* out = D in, full lattice. */
-void oracle_dw(const int *dims, double m0, const double *U_, const double *in_, double *out_) {
+void oracle_dw_c(const int *dims, double m0, const double *U_, const double *A_, const double *in_, double *out_) {
     lattice L;
     make_lattice(&L, dims, NULL);
     const cplx *U = (const cplx *)U_;
+    const cplx *A = (const cplx *)A_;
     const cplx *in = (const cplx *)in_;
     cplx *out = (cplx *)out_;
 #pragma omp parallel for schedule(static)
-    for (long s = 0; s < L.V; ++s) apply_site(&L, m0, U, in, s, 0, &out[12 * s]);
+    for (long s = 0; s < L.V; ++s) apply_site(&L, m0, U, A, in, s, 0, &out[12 * s]);
+}
+
+void oracle_dw(const int *dims, double m0, const double *U_, const double *in_, double *out_) {
+    oracle_dw_c(dims, m0, U_, NULL, in_, out_);
 }
 
 /* out = D^l in on every domain of the given colour (colour < 0: all domains);
  * sites outside the selected domains are set to zero.                        */
-void oracle_dw_local(const int *dims, const int *block, double m0, const double *U_, const double *in_,
-                     double *out_, int colour) {
+void oracle_dw_local_c(const int *dims, const int *block, double m0, const double *U_, const double *A_,
+                       const double *in_, double *out_, int colour) {
     lattice L;
     make_lattice(&L, dims, block);
     const cplx *U = (const cplx *)U_;
+    const cplx *A = (const cplx *)A_;
     const cplx *in = (const cplx *)in_;
     cplx *out = (cplx *)out_;
 #pragma omp parallel for schedule(static)
@@ -169,8 +187,13 @@ void oracle_dw_local(const int *dims, const int *block, double m0, const double 
             for (int a = 0; a < 12; ++a) out[12 * s + a] = 0;
             continue;
         }
-        apply_site(&L, m0, U, in, s, 1, &out[12 * s]);
+        apply_site(&L, m0, U, A, in, s, 1, &out[12 * s]);
     }
+}
+
+void oracle_dw_local(const int *dims, const int *block, double m0, const double *U_, const double *in_,
+                     double *out_, int colour) {
+    oracle_dw_local_c(dims, block, m0, U_, NULL, in_, out_, colour);
 }
 
 /* Lexicographic list of the sites of domain dom. */
@@ -234,14 +257,14 @@ static int dense_solve(cplx *A, cplx *rhs, int N) {
 /* Approximate (nmr >= 1: MR) or exact (nmr == 0) solve of D^l y = r on one
  * domain. rho, p are lattice-sized scratch vectors; only this domain's sites
  * are touched, so domains of one colour can be processed concurrently.       */
-static int local_solve(const lattice *L, double m0, const cplx *U, const long *sites, long ns, const cplx *r,
-                       cplx *y, cplx *rho, cplx *p, int nmr) {
+static int local_solve(const lattice *L, double m0, const cplx *U, const cplx *A, const long *sites, long ns,
+                       const cplx *r, cplx *y, cplx *rho, cplx *p, int nmr) {
     if (nmr == 0) {
         const int N = (int)(12 * ns);
-        cplx *A = (cplx *)calloc((size_t)N * N, sizeof(cplx));
+        cplx *Dl = (cplx *)calloc((size_t)N * N, sizeof(cplx)); /* dense D^l */
         cplx *x = (cplx *)malloc((size_t)N * sizeof(cplx));
-        if (!A || !x) {
-            free(A);
+        if (!Dl || !x) {
+            free(Dl);
             free(x);
             return -1;
         }
@@ -251,16 +274,16 @@ static int local_solve(const lattice *L, double m0, const cplx *U, const long *s
                 for (int a = 0; a < 12; ++a) rho[12 * sites[q] + a] = (12 * q + a == c) ? 1.0 : 0.0;
             for (long q = 0; q < ns; ++q) {
                 cplx o[12];
-                apply_site(L, m0, U, rho, sites[q], 1, o);
-                for (int a = 0; a < 12; ++a) A[(long)(12 * q + a) * N + c] = o[a];
+                apply_site(L, m0, U, A, rho, sites[q], 1, o);
+                for (int a = 0; a < 12; ++a) Dl[(long)(12 * q + a) * N + c] = o[a];
             }
         }
         for (long q = 0; q < ns; ++q)
             for (int a = 0; a < 12; ++a) x[12 * q + a] = r[12 * sites[q] + a];
-        const int rc = dense_solve(A, x, N);
+        const int rc = dense_solve(Dl, x, N);
         for (long q = 0; q < ns; ++q)
             for (int a = 0; a < 12; ++a) y[12 * sites[q] + a] = x[12 * q + a];
-        free(A);
+        free(Dl);
         free(x);
         return rc;
     }
@@ -270,7 +293,7 @@ static int local_solve(const lattice *L, double m0, const cplx *U, const long *s
             rho[12 * sites[q] + a] = r[12 * sites[q] + a];
         }
     for (int it = 0; it < nmr; ++it) {
-        for (long q = 0; q < ns; ++q) apply_site(L, m0, U, rho, sites[q], 1, &p[12 * sites[q]]);
+        for (long q = 0; q < ns; ++q) apply_site(L, m0, U, A, rho, sites[q], 1, &p[12 * sites[q]]);
         cplx prho = 0;
         double pp = 0;
         for (long q = 0; q < ns; ++q)
@@ -292,11 +315,12 @@ static int local_solve(const lattice *L, double m0, const cplx *U, const long *s
 
 /* SAP iteration (Algorithm 2): ncycles sweeps over colour 0 then colour 1,
  * starting from the x passed in (x is updated in place). Returns 0 on success. */
-int oracle_sap(const int *dims, const int *block, double m0, const double *U_, const double *b_, double *x_,
-               int ncycles, int nmr) {
+int oracle_sap_c(const int *dims, const int *block, double m0, const double *U_, const double *A_, const double *b_,
+                 double *x_, int ncycles, int nmr) {
     lattice L;
     make_lattice(&L, dims, block);
     const cplx *U = (const cplx *)U_;
+    const cplx *A = (const cplx *)A_;
     const cplx *b = (const cplx *)b_;
     cplx *x = (cplx *)x_;
     const long ndom = (long)L.nb[0] * L.nb[1] * L.nb[2] * L.nb[3];
@@ -321,10 +345,10 @@ int oracle_sap(const int *dims, const int *block, double m0, const double *U_, c
                 const long *sd = &sites[d * ns];
                 for (long q = 0; q < ns; ++q) {
                     cplx dx[12];
-                    apply_site(&L, m0, U, x, sd[q], 0, dx);
+                    apply_site(&L, m0, U, A, x, sd[q], 0, dx);
                     for (int a = 0; a < 12; ++a) r[12 * sd[q] + a] = b[12 * sd[q] + a] - dx[a];
                 }
-                err |= (local_solve(&L, m0, U, sd, ns, r, y, rho, p, nmr) != 0);
+                err |= (local_solve(&L, m0, U, A, sd, ns, r, y, rho, p, nmr) != 0);
             }
             /* update x^l <- x^l + y^l for every domain of this colour */
 #pragma omp parallel for schedule(static)
@@ -338,6 +362,97 @@ int oracle_sap(const int *dims, const int *block, double m0, const double *U_, c
     }
     free(r), free(y), free(rho), free(p), free(sites);
     return err ? -2 : 0;
+}
+
+int oracle_sap(const int *dims, const int *block, double m0, const double *U_, const double *b_, double *x_,
+               int ncycles, int nmr) {
+    return oracle_sap_c(dims, block, m0, U_, NULL, b_, x_, ncycles, nmr);
+}
+
+/* ---- clover term ---------------------------------------------------------- */
+
+/* c = op(a) op(b) for 3x3 complex matrices; op = dagger when the flag is set */
+static void mul3(const cplx *a, int da, const cplx *b, int db, cplx *c) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cplx acc = 0;
+            for (int k = 0; k < 3; ++k) {
+                const cplx x = da ? conj(a[3 * k + i]) : a[3 * i + k];
+                const cplx y = db ? conj(b[3 * j + k]) : b[3 * k + j];
+                acc += x * y;
+            }
+            c[3 * i + j] = acc;
+        }
+}
+
+/* product of four links, each optionally daggered, left to right */
+static void path4(const cplx *l[4], const int dag[4], cplx *out) {
+    cplx t1[9], t2[9];
+    mul3(l[0], dag[0], l[1], dag[1], t1);
+    mul3(t1, 0, l[2], dag[2], t2);
+    mul3(t2, 0, l[3], dag[3], out);
+}
+
+/* A[site][12][12] (complex) for the clover term with coefficient csw. */
+void oracle_clover(const int *dims, double csw, const double *U_, double *A_) {
+    lattice L;
+    make_lattice(&L, dims, NULL);
+    const cplx *U = (const cplx *)U_;
+    cplx *A = (cplx *)A_;
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < L.V; ++s) {
+        cplx a[12][12];
+        memset(a, 0, sizeof(a));
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                const long pm = hop(&L, s, mu, +1), mm = hop(&L, s, mu, -1);
+                const long pn = hop(&L, s, nu, +1), mn = hop(&L, s, nu, -1);
+                const long mp = hop(&L, mm, nu, +1);  /* n - mu + nu */
+                const long mmn = hop(&L, mm, nu, -1); /* n - mu - nu */
+                const long pmn = hop(&L, pm, nu, -1); /* n + mu - nu */
+#define LK(site, dir) (&U[36 * (site) + 9 * (dir)])
+                /* the four leaves around n, each in the (mu, nu) sense */
+                const cplx *l1[4] = {LK(s, mu), LK(pm, nu), LK(pn, mu), LK(s, nu)};
+                const int d1[4] = {0, 0, 1, 1};
+                const cplx *l2[4] = {LK(s, nu), LK(mp, mu), LK(mm, nu), LK(mm, mu)};
+                const int d2[4] = {0, 1, 1, 0};
+                const cplx *l3[4] = {LK(mm, mu), LK(mmn, nu), LK(mmn, mu), LK(mn, nu)};
+                const int d3[4] = {1, 1, 0, 0};
+                const cplx *l4[4] = {LK(mn, nu), LK(mn, mu), LK(pmn, nu), LK(s, mu)};
+                const int d4[4] = {1, 0, 0, 1};
+#undef LK
+                cplx Q[9] = {0}, t[9];
+                path4(l1, d1, t);
+                for (int i = 0; i < 9; ++i) Q[i] += t[i];
+                path4(l2, d2, t);
+                for (int i = 0; i < 9; ++i) Q[i] += t[i];
+                path4(l3, d3, t);
+                for (int i = 0; i < 9; ++i) Q[i] += t[i];
+                path4(l4, d4, t);
+                for (int i = 0; i < 9; ++i) Q[i] += t[i];
+                cplx F[9];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) F[3 * i + j] = (Q[3 * i + j] - conj(Q[3 * j + i])) / 8.0;
+                const cplx tr = (F[0] + F[4] + F[8]) / 3.0;
+                for (int i = 0; i < 3; ++i) F[4 * i] -= tr;
+                /* sigma_{mu nu} = (i/2)(g_mu g_nu - g_nu g_mu) */
+                cplx sig[4][4];
+                for (int p = 0; p < 4; ++p)
+                    for (int q = 0; q < 4; ++q) {
+                        cplx c = 0;
+                        for (int k = 0; k < 4; ++k)
+                            c += GAMMA[mu][p][k] * GAMMA[nu][k][q] - GAMMA[nu][p][k] * GAMMA[mu][k][q];
+                        sig[p][q] = 0.5 * I * c;
+                    }
+                for (int p = 0; p < 4; ++p)
+                    for (int q = 0; q < 4; ++q)
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = 0; j < 3; ++j)
+                                a[3 * p + i][3 * q + j] += 0.5 * csw * I * sig[p][q] * F[3 * i + j];
+            }
+        for (int i = 0; i < 12; ++i)
+            for (int j = 0; j < 12; ++j) A[144 * s + 12 * i + j] = a[i][j];
+    }
 }
 
 /* Domain colour of every site (0/1), for tests of the red-black structure. */
@@ -375,7 +490,7 @@ int oracle_mr_history(const int *dims, const int *block, double m0, const double
         /* MR from y = 0 is deterministic, so running it afresh with 1..nmr
          * steps reproduces the residual after each step.                     */
         for (int it = 1; it <= nmr; ++it) {
-            local_solve(&L, m0, U, sites, ns, r, y, rho, p, it);
+            local_solve(&L, m0, U, NULL, sites, ns, r, y, rho, p, it);
             for (long q = 0; q < ns; ++q)
                 for (int a = 0; a < 12; ++a)
                     norms[it] += creal(conj(rho[12 * sites[q] + a]) * rho[12 * sites[q] + a]);

@@ -376,3 +376,108 @@ def test_tune_m0_places_smallest_eigenvalue():
     ev = np.linalg.eigvals(_dense(U, dims, m0))
     # the leftmost eigenvalue of D_0 sits at Re = target after the shift
     assert abs(ev.real.min() - 1e-2) < 1e-6
+
+
+# --------------------------------------------------------------------------- clover term
+def _abelian_field(dims, b):
+    """U_{n,0} = diag(e^{i b n_1}, e^{-i b n_1}, 1), all other links 1: a uniform
+    field strength in the (0, 1) plane when b d_1 is a multiple of 2 pi."""
+    V = fg.volume(dims)
+    U = fg.unit_gauge(dims).copy()
+    y = coords(dims)[:, 1]
+    U[:, 0, 0, 0] = np.exp(1j * b * y)
+    U[:, 0, 1, 1] = np.exp(-1j * b * y)
+    assert U.shape == (V, 4, 3, 3)
+    return U
+
+
+def test_clover_free_field_vanishes():
+    dims = (4, 2, 4, 2)
+    A = oracle.clover(fg.unit_gauge(dims), dims, 1.7)
+    assert np.abs(A).max() == 0.0
+
+
+@pytest.mark.parametrize("csw", [1.0, 1.91])
+def test_clover_uniform_abelian_field_closed_form(csw):
+    """Every leaf of the (0,1) plane is diag(e^{-ib}, e^{ib}, 1), so
+    F_01 = diag(-i sin b, i sin b, 0) and the other planes vanish;
+    sigma_01 = (i/2)[gamma_0, gamma_1] = diag(-1, 1, -1, 1) in this basis
+    (gamma_0 gamma_1 = diag(i s3, i s3)), hence
+    A = (csw/2) diag(-1, 1, -1, 1) (x) diag(sin b, -sin b, 0)."""
+    dims = (2, 6, 2, 4)
+    b = 2 * np.pi / dims[1]
+    A = oracle.clover(_abelian_field(dims, b), dims, csw)
+    spin = np.array([-1.0, 1.0, -1.0, 1.0])
+    colour = np.array([1.0, -1.0, 0.0])
+    expect = np.diag(0.5 * csw * np.sin(b) * np.kron(spin, colour))
+    assert np.abs(A - expect[None]).max() < 1e-14
+    # the sigma_01 factor from the oracle's own gamma matrices agrees with the closed form
+    g = [oracle.gamma(mu) for mu in range(4)]
+    assert np.allclose(0.5j * (g[0] @ g[1] - g[1] @ g[0]), np.diag(spin))
+
+
+def test_clover_hermitian_chiral_and_gauge_covariant():
+    dims = (4, 2, 4, 4)
+    V = fg.volume(dims)
+    U = fg.gauge_field(dims, 0.7, seed=31)
+    A = oracle.clover(U, dims, 1.3)
+    assert np.abs(A - A.conj().transpose(0, 2, 1)).max() < 1e-15
+    g5 = np.kron(np.diag([1.0, 1.0, -1.0, -1.0]), np.eye(3))
+    assert np.abs(A @ g5 - g5 @ A).max() < 1e-15
+    assert np.abs(A).max() > 1e-2  # not trivially zero
+    g = fg.random_su3(V, 32)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        t = shift_index(dims, mu, +1)
+        Ug[:, mu] = g @ U[:, mu] @ g[t].conj().transpose(0, 2, 1)
+    G = np.einsum("xy,sab->sxayb", np.eye(4), g).reshape(V, 12, 12)
+    Ag = oracle.clover(Ug, dims, 1.3)
+    assert np.abs(Ag - G @ A @ G.conj().transpose(0, 2, 1)).max() < 1e-13
+
+
+def test_clover_operator_gamma5_hermitian_and_local_submatrix():
+    dims, block, m0 = SMALL_DIMS, SMALL_BLOCK, -0.4
+    V = fg.volume(dims)
+    U = fg.gauge_field(dims, 0.5, seed=33)
+    A = oracle.clover(U, dims, 1.91)
+    psi = fg.gaussian_source(dims, 34)
+    phi = fg.gaussian_source(dims, 35)
+    lhs = np.vdot(phi, G5 * oracle.dw(U, G5 * psi, dims, m0, A=A))
+    rhs = np.vdot(oracle.dw(U, phi, dims, m0, A=A), psi)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    # D_sw = D_w + block-diagonal A, and D_sw^l keeps the whole site term
+    Dsw = oracle.dense_operator(lambda v: oracle.dw(U, v.reshape(V, 4, 3), dims, m0, A=A).reshape(-1), 12 * V)
+    Dw = _dense(U, dims, m0)
+    blk = np.zeros_like(Dw)
+    for s_ in range(V):
+        blk[12 * s_:12 * s_ + 12, 12 * s_:12 * s_ + 12] = A[s_]
+    assert np.abs(Dsw - Dw - blk).max() < 1e-14
+    Dl = oracle.dense_operator(
+        lambda v: oracle.dw_local(U, v.reshape(V, 4, 3), dims, block, m0, A=A).reshape(-1), 12 * V)
+    dom, _ = _domain_index(dims, block)
+    sd = np.repeat(dom, 12)
+    assert np.abs(Dl - np.where(sd[:, None] == sd[None, :], Dsw, 0)).max() < 1e-14
+
+
+def test_clover_sap_exact_local_solves_equal_series():
+    """The series form of SAP (Sec. 3) holds for the clover-improved operator."""
+    dims, block, m0 = (4, 4, 4, 2), (2, 2, 2, 1), -0.5
+    U = fg.gauge_field(dims, 0.3, seed=0)
+    V = fg.volume(dims)
+    A = oracle.clover(U, dims, 1.91)
+    D = oracle.dense_operator(lambda v: oracle.dw(U, v.reshape(V, 4, 3), dims, m0, A=A).reshape(-1), 12 * V)
+    _, col = _domain_index(dims, block)
+    sc = np.repeat(col, 12)
+    perm = np.concatenate([np.where(sc == 0)[0], np.where(sc == 1)[0]])
+    Dp = D[np.ix_(perm, perm)]
+    h = (sc == 0).sum()
+    AL = Dp.copy()
+    AL[:h, h:] = 0
+    AU = -(Dp - AL)
+    ALi = np.linalg.inv(AL)
+    M = ALi + (ALi @ AU) @ ALi
+    v = fg.gaussian_source(dims, 36).reshape(-1)
+    z_series = np.empty_like(v)
+    z_series[perm] = M @ v[perm]
+    z = oracle.sap(U, v.reshape(V, 4, 3), dims, block, m0, 2, 0, A=A).reshape(-1)
+    assert np.linalg.norm(z - z_series) <= 1e-11 * np.linalg.norm(z_series)
