@@ -86,6 +86,21 @@ int dw_set_mass(dw_ctx* ctx, double m0);
  * internal storage precisions on first use; the caller's buffer is not kept. */
 int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device);
 
+/* Add the clover term of the improved operators of Sec. 5 (the paper cites
+ * the Sheikholeslami-Wohlert term without a formula; this is the standard
+ * site-diagonal form):
+ *   D_sw = D + A,  A_n = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}(n),
+ *   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F_{mu nu}(n) = (Q - Q^dagger)/8
+ *   made traceless, Q the sum of the four plaquettes in the (mu, nu) plane
+ *   that start and end at n, all in the same sense.
+ * The term is computed once on the device from the current gauge field (and
+ * again after every dw_set_gauge) and then enters dw_apply, sap_precondition
+ * (A is site-diagonal, so it is part of every local operator D^l) and
+ * fgmresdr_solve. csw = 0 restores the plain Wilson operator.
+ * Errors: DW_EINVAL (no gauge field yet, non-finite csw), DW_ENOMEM, DW_ECUDA;
+ * with the clover term, SAP domains are limited to 256 sites. */
+int dw_set_clover(dw_ctx* ctx, double csw);
+
 /* out = D in for nrhs spinor fields (Sec. 1, Eq. "Dw").
  * in, out: device pointers, canonical FP64 layout, nrhs*V*24 doubles each,
  * non-overlapping. prec selects the storage and arithmetic of the stencil:

@@ -74,6 +74,7 @@ _SIGS = {
     "dw_destroy": ([_P], None),
     "dw_set_mass": ([_P, ctypes.c_double], _I),
     "dw_set_gauge": ([_P, _P, _I], _I),
+    "dw_set_clover": ([_P, ctypes.c_double], _I),
     "dw_apply": ([_P, _P, _P, _I, _I], _I),
     "sap_precondition": ([_P, _P, _P, _I, _I, _I, _I], _I),
     "dw_default_params": ([ctypes.POINTER(dw_solver_params)], None),
@@ -155,6 +156,11 @@ def dw_set_mass(ctx, m0: float) -> None:
 
 def dw_set_gauge(ctx, U, on_device: bool) -> None:
     _check(_lib.dw_set_gauge(ctx, _ptr(U), int(bool(on_device))), "dw_set_gauge")
+
+
+def dw_set_clover(ctx, csw: float) -> None:
+    """Add the clover term with coefficient csw (0 restores plain Wilson)."""
+    _check(_lib.dw_set_clover(ctx, float(csw)), "dw_set_clover")
 
 
 def dw_apply(ctx, inp, out, prec: int = DW_F64, nrhs: int = 1) -> None:

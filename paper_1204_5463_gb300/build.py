@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libdwsolve.so")
-SOURCES = ["dw.cu", "sap.cu", "blas.cu", "solver.cpp", "dense.cpp", "api.cpp", "server.cpp", "noalloc.cu", "tune.cpp"]
+SOURCES = ["dw.cu", "sap.cu", "blas.cu", "clover.cu", "solver.cpp", "dense.cpp", "api.cpp", "server.cpp", "noalloc.cu",
+           "tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -1,6 +1,7 @@
 // C ABI of the library (include/dwsolve.h): contexts, the operator, the
 // preconditioner, the solver entry point, error reporting and profiling.
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -210,7 +211,30 @@ int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device) {
     for (int p = 0; p < 5; ++p) ctx->U_ready[p] = false;
     ctx->U_ready[P64] = true;
     ctx->have_gauge = true;
+    if (ctx->csw != 0.0 && (rc = dw_set_clover(ctx, ctx->csw))) return rc;  // the clover term follows the links
     DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return DW_OK;
+}
+
+int dw_set_clover(dw_ctx* ctx, double csw) {
+    if (!ctx) return fail(DW_EINVAL, "null context");
+    if (!std::isfinite(csw)) return fail(DW_EINVAL, "c_sw must be finite");
+    if (csw == 0.0) {
+        ctx->csw = 0.0;
+        return DW_OK;
+    }
+    if (!ctx->have_gauge) return fail(DW_EINVAL, "set the gauge field before the clover term");
+    const long long V = ctx->g.V;
+    int rc;
+    if ((rc = ctx->clov64.ensure((size_t)V * 72 * sizeof(double)))) return rc;
+    if ((rc = ctx->clov32.ensure((size_t)V * 72 * sizeof(float)))) return rc;
+    if ((rc = launch_clover_compute(ctx->g, ctx->U[P64].as<char>(), csw, ctx->clov64.as<double>(),
+                                    ctx->clov32.as<float4>(), ctx->stream)))
+        return rc;
+    DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->clov.a64 = ctx->clov64.as<char>();
+    ctx->clov.a32 = ctx->clov32.as<char>();
+    ctx->csw = csw;
     return DW_OK;
 }
 
@@ -230,7 +254,8 @@ int dw_apply(dw_ctx* ctx, const double* in, double* out, dw_prec prec, int nrhs)
         ProfScope ps(&ctx->prof, prec == DW_F64 ? "dw_f64" : prec == DW_F32 ? "dw_f32" : "dw_f16",
                      (double)nrhs * (2.0 * fb + link_bytes(prec, V)));
         FieldRef fi{ctx->work_in.as<char>(), fb, 0, 0}, fo{ctx->work_out.as<char>(), fb, 0, 0};
-        if ((rc = launch_dw(prec, prec, prec, ctx->g, ctx->m0, fi, fo, U, nullptr, nrhs, nullptr, ctx->stream)))
+        if ((rc = launch_dw(prec, prec, prec, ctx->g, ctx->m0, fi, fo, U, nullptr, nrhs, nullptr, ctx->stream,
+                            ctx->clover())))
             return rc;
     }
     if ((rc = launch_from_internal(prec, ctx->work_out.as<char>(), out, V, nrhs, ctx->stream))) return rc;
@@ -258,7 +283,7 @@ int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int n
             ProfScope ps(&ctx->prof, "sap_sweep",
                          (double)nrhs * 0.5 * (2.0 * fb + (mode == 2 ? fb : 0) + link_bytes(storage, V)));
             if ((rc = launch_sap_sweep(storage, storage, ctx->g, ctx->m0, fv, fx, U, nullptr, nrhs, colour, nmr, mode,
-                                       ctx->sap_threads[storage], ctx->stream)))
+                                       ctx->sap_threads[storage], ctx->stream, ctx->clover())))
                 return rc;
         }
     if ((rc = launch_from_internal(storage, ctx->work_out.as<char>(), z, V, nrhs, ctx->stream))) return rc;

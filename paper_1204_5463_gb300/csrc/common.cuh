@@ -43,6 +43,8 @@ template <class R>
 __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
     return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
 }
+template <class R>
+__device__ __forceinline__ cx<R> conj(cx<R> a) { return mk(a.re, -a.im); }
 // i * a and -i * a
 template <class R>
 __device__ __forceinline__ cx<R> ti(cx<R> a) { return mk(-a.im, a.re); }
@@ -483,6 +485,68 @@ __device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C>
     su3_mul<C, (SIGN < 0)>(u, h1, k1);
     reconstruct<MU, SIGN, C>(k0, k1, acc);
 }
+
+// ---------------------------------------------------------------------------
+// clover term (site-diagonal): per site two hermitian 6x6 blocks, chirality 0
+// acting on spinor components 0..5 (spins 0, 1) and chirality 1 on 6..11
+// (spins 2, 3). Each block is packed as 36 reals: the 6 (real) diagonal
+// entries, then the 15 entries above the diagonal, row by row, as (re, im).
+//   FP64 storage: double [72][V];   FP32 storage: float4 [18][V].
+// clover_acc<P>(A, V, s, in, acc, w): acc += w * (A_s in), in the compute
+// type C (double, float or double-float; FP64 storage feeds double and
+// double-float arithmetic, FP32 storage feeds float).
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+template <class C>
+__device__ __forceinline__ void clover_block(const C b[36], const cx<C>* x, cx<C>* acc, C w) {
+    cx<C> y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = b[i] * x[i];
+    int k = 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+            const cx<C> o = mk<C>(b[k], b[k + 1]);
+            k += 2;
+            y[i] = y[i] + o * x[j];
+            y[j] = y[j] + cmulc(o, x[i]);
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i] = acc[i] + w * y[i];
+}
+
+template <int P, class C>
+__device__ __forceinline__ void clover_acc(const char* A, long long V, long long s, const cx<C> in[12], cx<C> acc[12],
+                                           C w) {
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        C b[36];
+        if constexpr (P == P32) {
+            const float4* a = reinterpret_cast<const float4*>(A);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const float4 v = __ldg(&a[(long long)(9 * chi + q) * V + s]);
+                b[4 * q] = C(v.x);
+                b[4 * q + 1] = C(v.y);
+                b[4 * q + 2] = C(v.z);
+                b[4 * q + 3] = C(v.w);
+            }
+        } else {
+            const double* a = reinterpret_cast<const double*>(A);
+#pragma unroll
+            for (int q = 0; q < 36; ++q) {
+                const double v = __ldg(&a[(long long)(36 * chi + q) * V + s]);
+                if constexpr (std::is_same<C, df>::value)
+                    b[q] = df_from_double(v);
+                else
+                    b[q] = (C)v;
+            }
+        }
+        clover_block<C>(b, in + 6 * chi, acc + 6 * chi, w);
+    }
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // per-rhs field addressing for batched launches

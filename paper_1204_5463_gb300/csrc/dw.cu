@@ -100,9 +100,10 @@ __global__ void __launch_bounds__(kThreads) convert_kernel(FieldRef in, FieldRef
     store_spinor<PO, C>(field_ptr(out, jtab, r), V, s, v);
 }
 
-template <int PI, int PO, int PL, class C, bool SUB>
-__global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? ((PI == P32) ? 4 : 3) : 1) dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U,
-                                                      const int* jtab, int nrhs, FieldRef sub) {
+template <int PI, int PO, int PL, class C, bool SUB, bool CLOV>
+__global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? ((PI == P32) ? 4 : 3) : 1)
+    dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U, const int* jtab, int nrhs, FieldRef sub,
+              const char* clov) {
     const int r = blockIdx.x % nrhs;
     const long long s = (blockIdx.x / nrhs) * (long long)blockDim.x + threadIdx.x;
     if (s >= g.V || !rhs_active(jtab, r)) return;
@@ -130,6 +131,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? ((PI == P32) ? 4 
     DW_HOPS(3)
 #undef DW_HOPS
     load_spinor<PI, C>(pin, g.V, s, psi);
+    // clover term A psi_n, folded into the accumulator as -2 A psi_n
+    if constexpr (CLOV) clover_acc<(sizeof(C) == 4) ? P32 : P64, C>(clov, g.V, s, psi, acc, C(-2.0f));
     const C half = C(0.5f);
     cx<C> res[12];
     if constexpr (SUB) {
@@ -146,19 +149,43 @@ __global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? ((PI == P32) ? 4 
 
 dim3 site_grid(long long V, int nrhs) { return dim3((unsigned)((V + kThreads - 1) / kThreads), nrhs); }
 
+// every supported precision combination carries the clover term
+template <int PI, int PO, int PL, class C>
+constexpr bool clover_combo() {
+    return true;
+}
+
 template <int PI, int PO, int PL, class C>
 int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const char* U, const int* jtab, int nrhs,
-                    const FieldRef* sub, cudaStream_t st) {
+                    const FieldRef* sub, const ClovRef* cl, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.V + kThreads - 1) / kThreads) * (unsigned)nrhs;
     const C diag = C(4.0 + m0);
+    FieldRef none{};
+    const FieldRef sb = sub ? *sub : none;
+    if (cl) {
+        if constexpr (clover_combo<PI, PO, PL, C>()) {
+            const char* A = (sizeof(C) == 4) ? cl->a32 : cl->a64;
+            if (sub) {
+                if constexpr (PO == P64 || PO == PDF)
+                    dw_kernel<PI, PO, PL, C, true, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, A);
+                else
+                    return fail(DW_EINVAL, "residual stencil requires an FP64-class output");
+            } else {
+                dw_kernel<PI, PO, PL, C, false, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, A);
+            }
+            DW_LAUNCH_CHECK();
+            return DW_OK;
+        } else {
+            return fail(DW_EINVAL, "the clover term is not available for this precision combination");
+        }
+    }
     if (sub) {
         if constexpr (PO == P64 || PO == PDF)
-            dw_kernel<PI, PO, PL, C, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, *sub);
+            dw_kernel<PI, PO, PL, C, true, false><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, nullptr);
         else
             return fail(DW_EINVAL, "residual stencil requires an FP64-class output");
     } else {
-        FieldRef none{};
-        dw_kernel<PI, PO, PL, C, false><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, none);
+        dw_kernel<PI, PO, PL, C, false, false><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, nullptr);
     }
     DW_LAUNCH_CHECK();
     return DW_OK;
@@ -252,11 +279,11 @@ int launch_convert(int pin, int pout, FieldRef in, FieldRef out, long long V, co
 }
 
 int launch_dw(int pin, int pout, int plink, const Geom& g, double m0, FieldRef in, FieldRef out, const char* U,
-              const int* jtab, int nrhs, const FieldRef* sub, cudaStream_t st) {
+              const int* jtab, int nrhs, const FieldRef* sub, cudaStream_t st, const ClovRef* cl) {
     // Supported combinations: uniform precision (the stencil as an operator),
     // and low-precision input with an FP64 output (Arnoldi product w = D z).
 #define DWC(A, B, L, C)                                                                       \
-    if (pin == A && pout == B && plink == L) return dw_dispatch_sub<A, B, L, C>(g, m0, in, out, U, jtab, nrhs, sub, st);
+    if (pin == A && pout == B && plink == L) return dw_dispatch_sub<A, B, L, C>(g, m0, in, out, U, jtab, nrhs, sub, cl, st);
     DWC(P64, P64, P64, double)
     DWC(P32, P32, P32, float)
     DWC(P16, P16, P16, float)

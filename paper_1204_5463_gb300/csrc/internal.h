@@ -89,6 +89,15 @@ void release_workspace(Workspace* w);
 
 }  // namespace dwk
 
+namespace dwk {
+// The clover term of a context: FP64 storage (double [72][V]) for double and
+// double-float arithmetic, FP32 storage (float4 [18][V]) for float arithmetic.
+struct ClovRef {
+    const char* a64;
+    const char* a32;
+};
+}  // namespace dwk
+
 struct dw_ctx {
     dwk::Geom g;
     double m0 = 0.0;
@@ -101,6 +110,10 @@ struct dw_ctx {
     dwk::Profiler prof;
     std::vector<int> sap_threads;  // tuned launch shape per precision (0 = default)
     dwk::Workspace* ws = nullptr;  // solver workspace, kept between solves
+    double csw = 0.0;               // clover coefficient (0: plain Wilson operator)
+    dwk::DevBuf clov64, clov32;     // clover term, FP64 [72][V] and FP32 float4 [18][V]
+    dwk::ClovRef clov{nullptr, nullptr};
+    const dwk::ClovRef* clover() const { return csw != 0.0 ? &clov : nullptr; }
 };
 
 namespace dwk {
@@ -113,16 +126,21 @@ int launch_to_internal(int prec, const double* canon, char* out, long long V, in
 int launch_from_internal(int prec, const char* in, double* canon, long long V, int nrhs, cudaStream_t st);
 int launch_gauge_convert(int prec, const double* Ucanon, char* out, long long V, cudaStream_t st);
 int launch_link_convert(int prec, const char* U64, char* out, long long V, cudaStream_t st);
-// out = D in  (sub == nullptr)   or   out = sub - D in  (sub: FP64 field, PO must be P64)
+
+// out = D in  (sub == nullptr)   or   out = sub - D in  (sub: FP64 field, PO must be P64);
+// with cl, D includes the clover term
 int launch_dw(int pin, int pout, int plink, const Geom& g, double m0, FieldRef in, FieldRef out, const char* U,
-              const int* jtab, int nrhs, const FieldRef* sub, cudaStream_t st);
+              const int* jtab, int nrhs, const FieldRef* sub, cudaStream_t st, const ClovRef* cl = nullptr);
+// ----- clover.cu -----------------------------------------------------------
+int launch_clover_compute(const Geom& g, const char* U64, double csw, double* A64, float4* A32, cudaStream_t st);
 
 // ----- sap.cu --------------------------------------------------------------
 // One colour half-sweep of SAP (Algorithm 2) on every domain of `colour`:
 // r = v - D x (full operator), nmr MR steps on D^l y = r, x += y.
 // mode 0: x == 0 everywhere (r = v, x = y); 1: x == 0 on this colour; 2: general.
 int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
-                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st);
+                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st,
+                     const ClovRef* cl = nullptr);
 int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads);
 
 // ----- blas.cu -------------------------------------------------------------

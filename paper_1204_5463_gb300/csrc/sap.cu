@@ -172,10 +172,14 @@ __device__ __forceinline__ void block_sum3(C& a, C& b, C& c, C* red) {
     c = sc;
 }
 
-template <int PS, int PL, class C, int MAXT>
+// CLOV: the operator carries the clover term A (site-diagonal, so it is part
+// of D^l on every site): clov is its FP32 storage for float arithmetic and its
+// FP64 storage for double arithmetic.
+template <int PS, int PL, class C, int MAXT, bool CLOV>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref, const char* __restrict__ U, const int* jtab,
-                     int nrhs, int colour, int nmr, int mode) {
+                     int nrhs, int colour, int nmr, int mode, const char* __restrict__ clov) {
+    constexpr int CP = (sizeof(C) == 4) ? P32 : P64;  // storage of the clover term
     typedef LinkSh<PL> LS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x;
@@ -301,6 +305,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             const C half = (C)0.5;
             if (general) {
                 load_spinor<PS, C, false>(xsh, T, tid, psi);
+                if constexpr (CLOV) clover_acc<CP, C>(clov, g.V, s, psi, acc, (C)-2);  // A x as -2 A x in acc
 #pragma unroll
                 for (int c = 0; c < 12; ++c) rho[c] = rho[c] - (diag * psi[c] - half * acc[c]);
             } else {
@@ -345,6 +350,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             SAP_LOC_HOPS(2, ls2)
             SAP_LOC_HOPS(3, ls3)
 #undef SAP_LOC_HOPS
+            if constexpr (CLOV) clover_acc<CP, C>(clov, g.V, s, rho, acc, (C)-2);  // A rho as -2 A rho in acc
             const C half = (C)0.5;
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
@@ -384,7 +390,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
 
 template <int PS, int PL, class C>
 int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U, const int* jtab, int nrhs,
-                 int colour, int nmr, int mode, int threads, cudaStream_t st) {
+                 int colour, int nmr, int mode, int threads, cudaStream_t st, const ClovRef* cl) {
+    if (cl && threads > 256) return fail(DW_EINVAL, "the clover SAP sweep handles domains of at most 256 sites");
     const size_t smem = sizeof(C) * 24 * threads + (size_t)LinkSh<PL>::kBytes * threads + sizeof(C) * 3 * 32;
     // the shared-memory limit is a per-device property of the kernel: set it once per device
     static std::mutex mu;
@@ -394,9 +401,11 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
         DW_CUDA_TRY(cudaGetDevice(&dev));
         std::lock_guard<std::mutex> lock(mu);
         if (!done.count(dev)) {
-            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 256>,
+            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 256, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 1024>,
+            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 1024, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            DW_CUDA_TRY(cudaFuncSetAttribute(sap_sweep_kernel<PS, PL, C, 256, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
             done.insert(dev);
         }
@@ -417,12 +426,16 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const C diag = (C)(4.0 + m0);
-    if (threads <= 256)
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256>, g, diag, v, x, U, jtab, nrhs, colour,
-                                       nmr, mode));
+    const char* A = cl ? ((sizeof(C) == 4) ? cl->a32 : cl->a64) : nullptr;
+    if (cl)
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, true>, g, diag, v, x, U, jtab, nrhs,
+                                       colour, nmr, mode, A));
+    else if (threads <= 256)
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, false>, g, diag, v, x, U, jtab, nrhs,
+                                       colour, nmr, mode, A));
     else
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024>, g, diag, v, x, U, jtab, nrhs, colour,
-                                       nmr, mode));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024, false>, g, diag, v, x, U, jtab, nrhs,
+                                       colour, nmr, mode, A));
     DW_LAUNCH_CHECK();
     return DW_OK;
 }
@@ -438,20 +451,21 @@ int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads) {
 }
 
 int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
-                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st) {
+                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st,
+                     const ClovRef* cl) {
     if (threads <= 0) threads = ((g.B + 31) / 32) * 32;
     if (threads < g.B || threads % 32 != 0 || threads > 1024) return fail(DW_EINVAL, "bad SAP thread count");
     if (sap_smem_bytes(pspin, plink, g, threads) > 227 * 1024)
         return fail(DW_EINVAL, "SAP domain does not fit in shared memory at this precision");
     if (nmr < 1) return fail(DW_EINVAL, "nmr must be >= 1");
     if (pspin == P64 && plink == P64)
-        return sap_launch_t<P64, P64, double>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+        return sap_launch_t<P64, P64, double>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
     if (pspin == P32 && plink == P32)
-        return sap_launch_t<P32, P32, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+        return sap_launch_t<P32, P32, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
     if (pspin == P16 && plink == P16)
-        return sap_launch_t<P16, P16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+        return sap_launch_t<P16, P16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
     if (pspin == PB16 && plink == PB16)
-        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st);
+        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
     return fail(DW_EINVAL, "unsupported SAP precision combination");
 }
 

@@ -420,7 +420,7 @@ int Solver::cycle_end(int r) {
         ProfScope ps(&ctx->prof, "dw_f64_residual", ptr_bytes_dw(op, op, op, V) + fb);
         FieldRef in{xb + (long long)r * fb, 0, 0, 0}, out{rb + (long long)r * fb, 0, 0, 0},
             sub{bb + (long long)r * fb, 0, 0, 0};
-        if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, 1, &sub, st))) return rc;
+        if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, 1, &sub, st, ctx->clover()))) return rc;
     }
     explicit_res++;
     {
@@ -474,7 +474,7 @@ int Solver::step() {
             ProfScope ps(&ctx->prof, "sap_sweep", bytes);
             const int thr = (ctx->sap_threads.size() > (size_t)sp) ? ctx->sap_threads[sp] : 0;
             if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zs, U_sap, jtab_d, nrhs, colour, P.mr_steps, mode, thr,
-                                       st)))
+                                       st, ctx->clover())))
                 return rc;
         }
     if (zp != sp) {
@@ -485,7 +485,8 @@ int Solver::step() {
     {
         const int pl = (mp == P64) ? P64 : P32;
         ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(zp, vp, pl, V));
-        if ((rc = launch_dw(zp, vp, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st))) return rc;
+        if ((rc = launch_dw(zp, vp, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st, ctx->clover())))
+            return rc;
     }
     // classical Gram-Schmidt: h = V^H w, w' = w - V h; a second projection
     // ("twice is enough") only where cancellation could cost orthogonality at
@@ -630,7 +631,8 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
         }
         if ((rc = launch_to_internal(op, x_dev, xb, V, nrhs, st))) return rc;
         FieldRef in{xb, fb, 0, 0}, out{rb, fb, 0, 0}, sub{bb, fb, 0, 0};
-        if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st))) return rc;
+        if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st, ctx->clover())))
+            return rc;
         explicit_res++;
     } else {
         DW_CUDA_TRY(cudaMemsetAsync(xb, 0, (size_t)nrhs * fb, st));
