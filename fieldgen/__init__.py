@@ -136,14 +136,16 @@ def spectral_edges() -> dict:
         return json.load(f)
 
 
-def edge_key(dims, eps, seed) -> str:
-    return f"{'x'.join(map(str, dims))}_eps{eps}_seed{seed}"
+def edge_key(dims, eps, seed, csw=0.0) -> str:
+    k = f"{'x'.join(map(str, dims))}_eps{eps}_seed{seed}"
+    return k + (f"_csw{csw}" if csw else "")
 
 
-def tuned_m0(dims, eps, seed, target):
-    """Bare mass putting the left spectral edge of D at ``target``
-    (spec(D_m0) = spec(D_0) + m0), or None if the edge is not stored."""
-    e = spectral_edges().get(edge_key(dims, eps, seed))
+def tuned_m0(dims, eps, seed, target, csw=0.0):
+    """Bare mass putting the left spectral edge of D (with the clover term of
+    coefficient csw) at ``target`` (spec(D_m0) = spec(D_0) + m0), or None if
+    the edge is not stored."""
+    e = spectral_edges().get(edge_key(dims, eps, seed, csw))
     return None if e is None else target - e["edge_re"]
 
 
@@ -156,7 +158,7 @@ def lattice_configs():
     cfg = _configs()
     for c in cfg.values():
         if c.get("m0") is None:
-            c["m0"] = tuned_m0(c["dims"], c["eps"], c["seed"], c["target_min_abs_eig"])
+            c["m0"] = tuned_m0(c["dims"], c["eps"], c["seed"], c["target_min_abs_eig"], c.get("csw", 0.0))
     return cfg
 
 
@@ -170,6 +172,9 @@ def _configs():
         "mixed_32x32x32x64": dict(dims=(32, 32, 32, 64), eps=0.6, seed=0, m0=None,
                                   target_min_abs_eig=1e-3, block=(4, 4, 4, 4),
                                   sap_cycles=5, mr_steps=4, m=40, k=16, tol=1e-10, nrhs=1),
+        "clover_16x16x16x32": dict(dims=(16, 16, 16, 32), eps=0.5, seed=0, m0=None, csw=1.91,
+                                   target_min_abs_eig=1e-2, block=(4, 4, 4, 4),
+                                   sap_cycles=5, mr_steps=4, m=30, k=10, tol=1e-10, nrhs=1),
         "batched_24x24x24x48": dict(dims=(24, 24, 24, 48), eps=0.5, seed=0, m0=None,
                                     target_min_abs_eig=5e-3, block=(4, 4, 4, 4),
                                     sap_cycles=5, mr_steps=4, m=30, k=10, tol=1e-10, nrhs=12),

@@ -497,18 +497,20 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
     return theta, bound, matvecs
 
 
-def tune_m0_schur(U, dims, target: float, m: int = 60, k: int = 20, tol: float = 1e-3, seed: int = 0):
+def tune_m0_schur(U, dims, target: float, m: int = 60, k: int = 20, tol: float = 1e-3, seed: int = 0, clov=None):
     """As tune_m0_arnoldi with a thick-restarted Arnoldi (bounded memory)."""
     V = int(np.prod(dims))
     U = _cvec(U)
     t0 = time.time()
     theta, bound, mv = krylov_schur_edge(
-        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0).reshape(-1), 12 * V, m, k, tol=tol, seed=seed)
+        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0, A=clov).reshape(-1), 12 * V, m, k, tol=tol,
+        seed=seed)
     return target - theta.real, theta, bound, mv, time.time() - t0
 
 
-def tune_m0_arnoldi(U, dims, target: float, m: int = 200, seed: int = 0):
-    """Bare mass from the leftmost Ritz value of D at m0 = 0.
+def tune_m0_arnoldi(U, dims, target: float, m: int = 200, seed: int = 0, clov=None):
+    """Bare mass from the leftmost Ritz value of D at m0 = 0 (with the clover
+    term clov when given: it does not depend on m0).
 
     spec(D_m0) = spec(D_0) + m0, so m0 = target - Re(theta*) with theta* the
     Ritz value of smallest real part of an m-step Arnoldi process on D_0.
@@ -517,7 +519,7 @@ def tune_m0_arnoldi(U, dims, target: float, m: int = 200, seed: int = 0):
     U = _cvec(U)
     t0 = time.time()
     theta, bounds = arnoldi_ritz(
-        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0).reshape(-1), 12 * V, m, seed)
+        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0, A=clov).reshape(-1), 12 * V, m, seed)
     i = int(np.argmin(theta.real))
     return target - theta[i].real, theta[i], bounds[i], time.time() - t0
 

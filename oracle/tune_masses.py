@@ -36,8 +36,13 @@ FIELDS = [
   + [((24, 24, 24, 48), e, 0, 160) for e in (0.3, 0.45, 0.6)]
 
 
-def key(dims, eps, seed):
-    return f"{'x'.join(map(str, dims))}_eps{eps}_seed{seed}"
+# clover-improved operators: (dims, eps, seed, Arnoldi steps, c_sw)
+CLOVER_FIELDS = [((16, 16, 16, 32), 0.5, 0, 0, 1.91)]
+
+
+def key(dims, eps, seed, csw=0.0):
+    k = f"{'x'.join(map(str, dims))}_eps{eps}_seed{seed}"
+    return k + (f"_csw{csw}" if csw else "")
 
 
 def main():
@@ -48,20 +53,23 @@ def main():
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    for dims, eps, seed, m in FIELDS:
-        k = key(dims, eps, seed)
+    for dims, eps, seed, m, csw in [f + (0.0,) for f in FIELDS] + CLOVER_FIELDS:
+        k = key(dims, eps, seed, csw)
         if args.only and args.only != k:
             continue
         if k in data and data[k].get("arnoldi_steps") == m:
             continue
         t0 = time.time()
         U = fg.gauge_field(dims, eps, seed)
+        A = oracle.clover(U, dims, csw) if csw else None
         if m > 0:
-            _, theta, bound, secs = oracle.tune_m0_arnoldi(U, dims, 0.0, m=m)
+            _, theta, bound, secs = oracle.tune_m0_arnoldi(U, dims, 0.0, m=m, clov=A)
             how = {"arnoldi_steps": m}
         else:
-            _, theta, bound, mv, secs = oracle.tune_m0_schur(U, dims, 0.0, m=60, k=20, tol=2e-3)
+            _, theta, bound, mv, secs = oracle.tune_m0_schur(U, dims, 0.0, m=60, k=20, tol=2e-3, clov=A)
             how = {"arnoldi_steps": 0, "krylov_schur": {"m": 60, "k": 20, "tol": 2e-3, "matvecs": mv}}
+        if csw:
+            how["csw"] = csw
         data[k] = {"dims": list(dims), "eps": eps, "seed": seed, **how,
                    "edge_re": float(theta.real), "edge_im": float(theta.imag), "ritz_residual_bound": float(bound),
                    "seconds": round(time.time() - t0, 1)}
