@@ -183,6 +183,24 @@ def oracle_sample(cfg, U, b, n_iter):
     return dt / max(1, res.iterations), res.iterations
 
 
+def max_over_ranks(values, dist=None, device="cuda"):
+    """The maximum over all ranks of each value (a no-op without a process
+    group): replica timings are taken as the slowest rank's."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(units_per_rank, seconds, world):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -435,7 +453,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        # the reference arm runs the CPU oracle: gloo, no device
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.serving:
         return run_serving(args, rank, world)
@@ -519,11 +539,8 @@ def main():
     dw.dw_profile(ctx, False)
     ms_prof = pe0.elapsed_time(pe1)
     ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms, ms_prof], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_prof = float(t[0].item()), float(t[1].item())
-    value = args.steps * world / (ms / 1e3)
+    ms, ms_prof = max_over_ranks([ms, ms_prof], dist)
+    value = replica_throughput(args.steps, ms / 1e3, world)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     bh = torch.from_numpy(np.ascontiguousarray(b).view(np.float64).reshape(-1).copy()).pin_memory()
@@ -538,11 +555,8 @@ def main():
         dw.fgmresdr_solve(ctx, bh.data_ptr(), xh.data_ptr(), Ph)
     barrier()
     e2e_s = time.perf_counter() - e0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = args.steps * world / e2e_s
+    (e2e_s,) = max_over_ranks([e2e_s], dist)
+    e2e_value = replica_throughput(args.steps, e2e_s, world)
 
     # the same lattice, 12 right-hand sides per launch, FP16 SAP storage: the
     # mixed-precision batched solver against the plain single-rhs one above
@@ -563,12 +577,8 @@ def main():
             assert S12.converged == 12
         m1e.record(stream)
         barrier()
-        mms = m0e.elapsed_time(m1e)
-        if dist:
-            t = torch.tensor([mms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            mms = float(t.item())
-        mb_value = 12 * nb_steps * world / (mms / 1e3)
+        (mms,) = max_over_ranks([m0e.elapsed_time(m1e)], dist)
+        mb_value = replica_throughput(12 * nb_steps, mms / 1e3, world)
         mb = {"value": mb_value, "unit": "solves/s", "nrhs": 12, "sap_prec": "f16", "steps": nb_steps,
               "ms_per_step": mms / nb_steps, "iterations_max": S12.iterations,
               "true_rel_res_max": max(S12.true_rel_res[i] for i in range(12)), "ratio_vs_plain": mb_value / value}
@@ -584,12 +594,8 @@ def main():
             assert S12.converged == 12
         m1e.record(stream)
         barrier()
-        mms = m0e.elapsed_time(m1e)
-        if dist:
-            t = torch.tensor([mms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            mms = float(t.item())
-        v2 = 12 * nb_steps * world / (mms / 1e3)
+        (mms,) = max_over_ranks([m0e.elapsed_time(m1e)], dist)
+        v2 = replica_throughput(12 * nb_steps, mms / 1e3, world)
         mb["f32_basis"] = {"value": v2, "unit": "solves/s", "ms_per_step": mms / nb_steps,
                            "iterations_max": S12.iterations,
                            "true_rel_res_max": max(S12.true_rel_res[i] for i in range(12)),
@@ -612,12 +618,8 @@ def main():
             assert S32.converged == 1 and S32.true_rel_res[0] <= cfg["tol"]
         s1e.record(stream)
         barrier()
-        sms = s0e.elapsed_time(s1e)
-        if dist:
-            t = torch.tensor([sms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sms = float(t.item())
-        sv = args.steps * world / (sms / 1e3)
+        (sms,) = max_over_ranks([s0e.elapsed_time(s1e)], dist)
+        sv = replica_throughput(args.steps, sms / 1e3, world)
         sp32 = {"value": sv, "unit": "solves/s", "outer_prec": "f32 basis, double-float x/b/r",
                 "ms_per_step": sms / args.steps, "iterations": S32.iterations, "cycles": S32.cycles,
                 "clean_restarts": S32.clean_restarts, "true_rel_res": S32.true_rel_res[0],
@@ -642,12 +644,8 @@ def main():
             assert Sc.converged == 1 and Sc.true_rel_res[0] <= ccfg["tol"]
         c1e.record(stream)
         barrier()
-        cms = c0e.elapsed_time(c1e)
-        if dist:
-            t = torch.tensor([cms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            cms = float(t.item())
-        cv = args.steps * world / (cms / 1e3)
+        (cms,) = max_over_ranks([c0e.elapsed_time(c1e)], dist)
+        cv = replica_throughput(args.steps, cms / 1e3, world)
         clov = {"value": cv, "unit": "solves/s", "csw": ccfg["csw"], "m0": ccfg["m0"],
                 "ms_per_step": cms / args.steps, "iterations": Sc.iterations, "cycles": Sc.cycles,
                 "clean_restarts": Sc.clean_restarts, "true_rel_res": Sc.true_rel_res[0]}
