@@ -227,7 +227,8 @@ int dw_autotune_block(const dw_lattice* L, const double* U, const double* b, con
  * that forbid device allocation, processes with a fixed memory budget).
  *
  * out = D in with FP32 storage and arithmetic, exactly as dw_apply(..., DW_F32,
- * 1) computes it, but without a context and without allocating anything: the
+ * 1) computes it for the plain Wilson operator (there is no context, so no
+ * clover term), but without allocating anything: the
  * FP32 copies of the links and of the fields live in one file-scope device
  * array of 2 MiB (480 bytes per site), so the lattice may have at most 4096
  * sites (larger lattices return DW_EINVAL). dims: the four extents (no domain
@@ -275,9 +276,12 @@ typedef struct {
 
 typedef struct dw_server dw_server;
 
-/* Estimated device bytes of a request: gauge copies (FP64 + FP32 [+ SAP
- * storage]) + upload staging + per rhs ((m+1) outer vectors + m SAP-storage
- * vectors + x, b, r + SAP input + host staging) + k rotation scratch. */
+/* Estimated device bytes of a request: gauge copies (FP64 + FP32 [+ 16-bit
+ * SAP storage] [+ double-float for the residual stencil]) + upload staging +
+ * per rhs ((m+1) Arnoldi vectors in the basis format + m Z vectors (FP32 when
+ * a 16-bit SAP is deflated, with the SAP output buffer) + x, b, r + SAP input
+ * [+ FP32 residual copy for an FP32 basis] + host staging) + k rotation
+ * scratch. Requests solve the plain Wilson operator. */
 size_t dw_request_bytes(const dw_request* r);
 
 /* Creates the server on the current device with max_slots worker threads. */
