@@ -420,7 +420,10 @@ __global__ void __launch_bounds__(kT) scale_kernel(const double2* src, double2* 
 }
 
 // ---- in-place rotation of flat columns: X_c = sum_i X_i Q[i][c] (c < kout) ----
-template <int VP>
+// KMAX: the accumulators held per thread (kout <= KMAX); instantiated for a
+// few sizes so that a small deflation space does not pay the registers (and
+// the occupancy) of the largest
+template <int VP, int KMAX>
 __global__ void __launch_bounds__(kT) rotate_outer_kernel(double2* X, long long rs, long long cs, long long n,
                                                           const int* active, int nin, int kout, const double2* Q,
                                                           int qld) {
@@ -435,17 +438,17 @@ __global__ void __launch_bounds__(kT) rotate_outer_kernel(double2* X, long long 
     __syncthreads();
     double2* Xr = X + r * rs;
     for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
-        C acc[kRotMax];
+        C acc[KMAX];
 #pragma unroll
-        for (int c = 0; c < kRotMax; ++c) acc[c] = E::zero();
+        for (int c = 0; c < KMAX; ++c) acc[c] = E::zero();
         for (int i = 0; i < nin; ++i) {
             const C v = E::load_rw(Xr + (long long)i * cs, e);
 #pragma unroll
-            for (int c = 0; c < kRotMax; ++c)
+            for (int c = 0; c < KMAX; ++c)
                 if (c < kout) E::mac(acc[c], q[i * kout + c], v);
         }
 #pragma unroll
-        for (int c = 0; c < kRotMax; ++c)
+        for (int c = 0; c < KMAX; ++c)
             if (c < kout) E::store(Xr + (long long)c * cs, e, E::fin(acc[c]));
     }
 }
@@ -697,12 +700,21 @@ int launch_rotate(int prec, char* X, long long rhs_stride, long long col_stride,
     const long long n = 12 * V;
     if (prec == P64 || prec == PDF) {
         double2* Xd = reinterpret_cast<double2*>(X);
-        if (prec == PDF)
-            rotate_outer_kernel<PDF><<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(Xd, rhs_stride / 16, col_stride / 16,
-                                                                             n, active, nin, kout, Q, qld);
-        else
-            rotate_outer_kernel<P64><<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(Xd, rhs_stride / 16, col_stride / 16,
-                                                                             n, active, nin, kout, Q, qld);
+        const dim3 grid(grid_for(n), nrhs);
+        const long long rs = rhs_stride / 16, cs = col_stride / 16;
+#define ROT(K)                                                                                              \
+    if (kout <= K) {                                                                                        \
+        if (prec == PDF)                                                                                    \
+            rotate_outer_kernel<PDF, K><<<grid, kT, qsm, st>>>(Xd, rs, cs, n, active, nin, kout, Q, qld);   \
+        else                                                                                                \
+            rotate_outer_kernel<P64, K><<<grid, kT, qsm, st>>>(Xd, rs, cs, n, active, nin, kout, Q, qld);   \
+        DW_LAUNCH_CHECK();                                                                                  \
+        return DW_OK;                                                                                       \
+    }
+        ROT(6)
+        ROT(11)
+        ROT(kRotMax)
+#undef ROT
     } else if (prec == P32) {
         rotate_f32_kernel<<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(reinterpret_cast<float2*>(X), rhs_stride / 8,
                                                                     col_stride / 8, n, active, nin, kout, Q, qld);
