@@ -167,9 +167,28 @@ def dw_bandwidth(peaks, reps=10):
         gbs = d["bytes"] / d["launches"] / avg_s / 1e9
         out[name] = {"GB/s": gbs, "frac": gbs / peaks["hbm_gbs"], "avg_us": avg_s * 1e6,
                      "bytes_per_site": d["bytes"] / d["launches"] / fg.volume(dims),
+                     "Gsites_per_s": fg.volume(dims) / avg_s / 1e9,
                      "traffic": kernel_traffic("dw_" + name)}
     dw.dw_destroy(ctx)
     return out
+
+
+def oracle_kernels(cfg, U, b):
+    """The oracle's D (GB/s at the FP64 algorithmic 960 B/site) and one SAP
+    application (s cycles) on this workload, timed on the host cores."""
+    import oracle
+
+    V = 1
+    for d in cfg["dims"]:
+        V *= d
+    oracle.dw(U, b, cfg["dims"], cfg["m0"])  # builds / loads the oracle
+    t0 = time.perf_counter()
+    oracle.dw(U, b, cfg["dims"], cfg["m0"])
+    t_dw = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.sap(U, b, cfg["dims"], cfg["block"], cfg["m0"], cfg["sap_cycles"], cfg["mr_steps"])
+    t_sap = time.perf_counter() - t0
+    return {"dw_GB/s": 960.0 * V / t_dw / 1e9, "dw_s": t_dw, "sap_application_s": t_sap}
 
 
 def oracle_sample(cfg, U, b, n_iter):
@@ -707,7 +726,8 @@ def main():
         line["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores(), "kind": "oracle",
                                 "sample": f"{n} Arnoldi steps of the FP64 oracle on this workload "
                                           f"({t_it:.2f} s/step), extrapolated to the GPU solve's "
-                                          f"{int(statistics.median(iters))} steps"}
+                                          f"{int(statistics.median(iters))} steps",
+                                "kernels": oracle_kernels(cfg, U, b)}
     dw.dw_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
