@@ -124,9 +124,9 @@ def kernel_traffic(name):
     return e["bytes_per_launch"] * e.get("scale", 1.0)
 
 
-def dw_bandwidth(peaks, reps=10):
-    """The full-lattice stencil alone on a 24^3 x 48 lattice (its links and
-    fields, 318 MB in FP32, exceed L2): algorithmic bytes per site (links +
+def dw_bandwidth(peaks, reps=10, dims=(24, 24, 24, 48)):
+    """The full-lattice stencil alone on a 24^3 x 48 lattice by default (its
+    links and fields, 318 MB in FP32, exceed L2): algorithmic bytes per site (links +
     input + output: 960 B FP64, 480 B FP32, 248 B FP16 with scales) over the
     kernel's CUDA-event time, per storage precision. L2 is flushed (a 256 MB
     write) before every call; each call converts its input to the internal
@@ -137,7 +137,7 @@ def dw_bandwidth(peaks, reps=10):
     import fieldgen as fg
     import paper_1204_5463_gb300 as dw
 
-    dims = (24, 24, 24, 48)
+    dims = tuple(dims)
     U = fg.gauge_field(dims, 0.5, 0)
     psi = fg.gaussian_source(dims, 7)
     stream = torch.cuda.current_stream()
@@ -449,6 +449,7 @@ def main():
     ap.add_argument("--sap-prec", default="f32")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-dw-bw", action="store_true", help="skip the stand-alone D_w bandwidth measurement")
+    ap.add_argument("--dw-lattice", default="24x24x24x48", help="lattice of the stand-alone D_w measurement")
     ap.add_argument("--serving", action="store_true", help="run the serving measurement instead")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
@@ -692,7 +693,7 @@ def main():
     roof.update({"kernel": dom, "traffic": tr, "launches": d["launches"], "avg_us": 1e3 * avg_ms})
     shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4) for k, v in prof.items()}
     avg_us = {k: round(1e3 * v["total_ms"] / v["launches"], 2) for k, v in prof.items() if v["launches"]}
-    dwbw = None if args.no_dw_bw else dw_bandwidth(peaks)
+    dwbw = None if args.no_dw_bw else dw_bandwidth(peaks, dims=tuple(int(v) for v in args.dw_lattice.split("x")))
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
