@@ -169,3 +169,30 @@ def test_clover_sap_rejects_large_domains(dw):
         assert ei.value.code == dw.DW_EINVAL
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("outer", [4, 1])
+def test_clover_batched_equals_single(dw, outer):
+    """Several right-hand sides per launch (column tables in the SAP sweeps,
+    the Arnoldi product and the residual) give the single-rhs iterates."""
+    cfg = fg.lattice_configs()["tiny_4x4x4x4"]
+    dims = cfg["dims"]
+    U = fg.gauge_field(dims, cfg["eps"], cfg["seed"])
+    bs = fg.gaussian_source(dims, 9, nrhs=3)
+    c = Ctx(dw, dims, cfg["block"], cfg["m0"], U)
+    try:
+        P = dw.dw_default_params(m=cfg["m"], k=3, tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                                 mr_steps=cfg["mr_steps"], sap_prec=1, matvec_prec=1, outer_prec=outer, nrhs=3)
+        xb = torch.zeros(bs.size * 2, dtype=torch.float64, device="cuda")
+        Sb = dw.fgmresdr_solve(c.h, dev(bs), xb, P)
+        xbh = host(xb, bs.shape)
+        assert Sb.converged == 3
+        for r in range(3):
+            P1 = dw.dw_default_params(m=cfg["m"], k=3, tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                                      mr_steps=cfg["mr_steps"], sap_prec=1, matvec_prec=1, outer_prec=outer)
+            x1 = torch.zeros(bs[r].size * 2, dtype=torch.float64, device="cuda")
+            S1 = dw.fgmresdr_solve(c.h, dev(bs[r]), x1, P1)
+            assert S1.iterations == Sb.iterations_rhs[r]
+            assert rel2(xbh[r].reshape(-1), host(x1, bs[r].shape).reshape(-1)) <= 1e-12
+    finally:
+        c.close()
