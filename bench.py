@@ -304,7 +304,7 @@ def run_serving(args, rank, world):
             if dt > 0:
                 time.sleep(dt)
             P = dw.dw_default_params(m=30, k=10, tol=1e-10, sap_cycles=5, mr_steps=4, sap_prec=dw.DW_F16,
-                                     nrhs=q["nrhs"])
+                                     nrhs=q["nrhs"], outer_prec=dw.PREC[args.serving_outer])
             r = dw.make_request(q["dims"], (4, 4, 4, 4), q["m0"], fields[(q["dims"], q["eps"])], q["b"], q["x"], P)
             keep.append(r)
             ids[i] = dw.dw_server_submit(srv, r)
@@ -329,7 +329,9 @@ def run_serving(args, rank, world):
         "offered_req_per_s": args.rate, "achieved_req_per_s": len(reqs) / wall, "wall_s": wall,
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(max(lat))},
-        "peak_hbm_gb": info["peak_bytes"] / 1e9, "slots": args.slots, "dtype": "f16 SAP, f32 D z, double-float Arnoldi basis and residual",
+        "peak_hbm_gb": info["peak_bytes"] / 1e9, "slots": args.slots,
+        "dtype": "f16 SAP, f32 D z, " + ("FP32 Arnoldi basis with double-float residual" if args.serving_outer == "f32"
+                                         else "double-float Arnoldi basis and residual"),
         "data": "synthetic",
         "config": {"workload": "serving: volumes {8^3x16,16^3x32,24^3x48}, eps {0.3,0.6}, "
                                "min|lambda| log-uniform [1e-3,1e-2], 1-12 rhs, tol 1e-10, m 30, k 10, SAP 5x4"},
@@ -454,6 +456,8 @@ def main():
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serving-outer", default="df64", choices=["df64", "f32"],
+                    help="Arnoldi basis of the served solves (f32: the single-precision scheme of Sec. 4.7)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="wilson_16x16x16x32 (default, the benchmark line), batched_24x24x24x48, mixed_32x32x32x64, "
                          "sap_standalone (SAP as a solver around the spectral edge, 16^3x32)")
