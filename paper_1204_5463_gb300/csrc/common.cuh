@@ -412,8 +412,35 @@ __device__ __forceinline__ void load_link(const char* base, long long V, int mu,
 // hop<MU, SIGN>(psi, U, acc): acc += (1 + SIGN gamma_MU) W psi with W = U for
 // SIGN = +1 and W = U^dagger for SIGN = -1.
 // ---------------------------------------------------------------------------
-template <class C, bool DAG>
+// PACK (FP32 only): the complex products as paired FP32 FMAs on (re, im),
+// w h = w.re (h) + w.im (i h), two paired FMAs per complex product (for
+// U^dagger, conj(w) h = w.re h + w.im (-i h)). It saves issue slots where the
+// registers allow (the SAP sweeps: 5% faster batched); in the stand-alone
+// stencil, capped at 64-80 registers, it spills and loses.
+template <class C, bool DAG, bool PACK = false>
 __device__ __forceinline__ void su3_mul(const cx<C> u[9], const cx<C> h[3], cx<C> k[3]) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    if constexpr (PACK && std::is_same<C, float>::value) {
+        float2 hp[3], hr[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            hp[b] = make_float2(h[b].re, h[b].im);
+            hr[b] = DAG ? make_float2(h[b].im, -h[b].re) : make_float2(-h[b].im, h[b].re);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const cx<float> w = DAG ? u[3 * b + a] : u[3 * a + b];
+                acc = __ffma2_rn(make_float2(w.re, w.re), hp[b], acc);
+                acc = __ffma2_rn(make_float2(w.im, w.im), hr[b], acc);
+            }
+            k[a] = mk<float>(acc.x, acc.y);
+        }
+        return;
+    }
+#endif
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         cx<C> acc;
@@ -477,12 +504,12 @@ __device__ __forceinline__ void reconstruct(const cx<C> k0[3], const cx<C> k1[3]
     }
 }
 
-template <int MU, int SIGN, class C>
+template <int MU, int SIGN, class C, bool PACK = false>
 __device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C> acc[12]) {
     cx<C> h0[3], h1[3], k0[3], k1[3];
     project<MU, SIGN, C>(psi, h0, h1);
-    su3_mul<C, (SIGN < 0)>(u, h0, k0);
-    su3_mul<C, (SIGN < 0)>(u, h1, k1);
+    su3_mul<C, (SIGN < 0), PACK>(u, h0, k0);
+    su3_mul<C, (SIGN < 0), PACK>(u, h1, k1);
     reconstruct<MU, SIGN, C>(k0, k1, acc);
 }
 

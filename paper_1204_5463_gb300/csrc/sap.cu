@@ -276,25 +276,25 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             if (general) {                                                                   \
                 load_spinor<PS, C, false>(xsh, T, tid + LS_MU, psi);                         \
                 LS::template load<C>(lsh, T, MU, tid, u);                                    \
-                hop<MU, +1, C>(psi, u, acc);                                                 \
+                hop<MU, +1, C, true>(psi, u, acc);                                                 \
             }                                                                                \
         } else {                                                                             \
             load_spinor<PS, C>(xb, g.V, neighbour(g, s, xg, MU, +1), psi);                   \
             LS::template load<C>(lsh, T, MU, tid, u);                                        \
-            hop<MU, +1, C>(psi, u, acc);                                                     \
+            hop<MU, +1, C, true>(psi, u, acc);                                                     \
         }                                                                                    \
         if (lx[MU] >= 1) {                                                                   \
             if (general) {                                                                   \
                 const int tn = tid - LS_MU;                                                  \
                 load_spinor<PS, C, false>(xsh, T, tn, psi);                                  \
                 LS::template load<C>(lsh, T, MU, tn, u);                                     \
-                hop<MU, -1, C>(psi, u, acc);                                                 \
+                hop<MU, -1, C, true>(psi, u, acc);                                                 \
             }                                                                                \
         } else {                                                                             \
             const long long sm = neighbour(g, s, xg, MU, -1);                                \
             load_spinor<PS, C>(xb, g.V, sm, psi);                                            \
             load_link<PL, C>(U, g.V, MU, sm, u);                                             \
-            hop<MU, -1, C>(psi, u, acc);                                                     \
+            hop<MU, -1, C, true>(psi, u, acc);                                                     \
         }                                                                                    \
     }
             SAP_RES_HOPS(0, 1)
@@ -336,13 +336,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
         if (lx[MU] + 1 < g.b[MU]) {                                                           \
             rho_load<C>(rsh, T, tid + LS_MU, psi);                                            \
             LS::template load<C>(lsh, T, MU, tid, u);                                         \
-            hop<MU, +1, C>(psi, u, acc);                                                      \
+            hop<MU, +1, C, true>(psi, u, acc);                                                      \
         }                                                                                     \
         if (lx[MU] >= 1) {                                                                    \
             const int tn = tid - LS_MU;                                                       \
             rho_load<C>(rsh, T, tn, psi);                                                     \
             LS::template load<C>(lsh, T, MU, tn, u);                                          \
-            hop<MU, -1, C>(psi, u, acc);                                                      \
+            hop<MU, -1, C, true>(psi, u, acc);                                                      \
         }                                                                                     \
     }
             SAP_LOC_HOPS(0, 1)
