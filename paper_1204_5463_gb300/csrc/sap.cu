@@ -270,32 +270,34 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             for (int c = 0; c < 12; ++c) acc[c] = czero<C>();
             const bool general = (mode == 2);
             const char* xsh = reinterpret_cast<const char*>(rsh);
+    // an interior neighbour is read from shared memory and a boundary one
+    // through L2; the branches differ only in the loads, so each direction
+    // runs one hop for the whole warp
 #define SAP_RES_HOPS(MU, LS_MU)                                                              \
     {                                                                                        \
-        if (lx[MU] + 1 < g.b[MU]) {                                                          \
-            if (general) {                                                                   \
-                load_spinor<PS, C, false>(xsh, T, tid + LS_MU, psi);                         \
-                LS::template load<C>(lsh, T, MU, tid, u);                                    \
-                hop<MU, +1, C, true>(psi, u, acc);                                                 \
-            }                                                                                \
+        const bool inp = lx[MU] + 1 < g.b[MU];                                               \
+        if (inp) {                                                                           \
+            if (general) load_spinor<PS, C, false>(xsh, T, tid + LS_MU, psi);                \
         } else {                                                                             \
             load_spinor<PS, C>(xb, g.V, neighbour(g, s, xg, MU, +1), psi);                   \
-            LS::template load<C>(lsh, T, MU, tid, u);                                        \
-            hop<MU, +1, C, true>(psi, u, acc);                                                     \
         }                                                                                    \
-        if (lx[MU] >= 1) {                                                                   \
+        if (general || !inp) {                                                               \
+            LS::template load<C>(lsh, T, MU, tid, u);                                        \
+            hop<MU, +1, C, true>(psi, u, acc);                                               \
+        }                                                                                    \
+        const bool inm = lx[MU] >= 1;                                                        \
+        if (inm) {                                                                           \
             if (general) {                                                                   \
                 const int tn = tid - LS_MU;                                                  \
                 load_spinor<PS, C, false>(xsh, T, tn, psi);                                  \
                 LS::template load<C>(lsh, T, MU, tn, u);                                     \
-                hop<MU, -1, C, true>(psi, u, acc);                                                 \
             }                                                                                \
         } else {                                                                             \
             const long long sm = neighbour(g, s, xg, MU, -1);                                \
             load_spinor<PS, C>(xb, g.V, sm, psi);                                            \
             load_link<PL, C>(U, g.V, MU, sm, u);                                             \
-            hop<MU, -1, C, true>(psi, u, acc);                                                     \
         }                                                                                    \
+        if (general || !inm) hop<MU, -1, C, true>(psi, u, acc);                              \
     }
             SAP_RES_HOPS(0, 1)
             SAP_RES_HOPS(1, ls1)
