@@ -277,7 +277,8 @@ typedef struct {
 typedef struct dw_server dw_server;
 
 /* Estimated device bytes of a request: gauge copies (FP64 + FP32 [+ 16-bit
- * SAP storage] [+ double-float for the residual stencil]) + upload staging +
+ * SAP storage] [+ double-float for the residual stencil] + the SAP links
+ * packed per domain) + upload staging +
  * per rhs ((m+1) Arnoldi vectors in the basis format + m Z vectors (FP32 when
  * a 16-bit SAP is deflated, with the SAP output buffer) + x, b, r + SAP input
  * [+ FP32 residual copy for an FP32 basis] + host staging) + k rotation

@@ -129,6 +129,41 @@ int gauge_for(dw_ctx* ctx, int prec, const char** out) {
     return DW_OK;
 }
 
+int HostFlag::ensure() {
+    if (h) return DW_OK;
+    int* p = nullptr;
+    DW_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&p), sizeof(int), cudaHostAllocMapped));
+    *p = 0;
+    h = p;
+    DW_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), p, 0));
+    return DW_OK;
+}
+
+HostFlag::~HostFlag() {
+    if (h) cudaFreeHost(h);
+}
+
+int sap_links_for(dw_ctx* ctx, int prec, int threads, const char** U, const char** img) {
+    int rc;
+    if ((rc = gauge_for(ctx, prec, U))) return rc;
+    if ((rc = ctx->sap_err.ensure())) return rc;
+    threads = sap_threads(ctx->g, threads);
+    if (ctx->Uimg_threads[prec] != threads) {
+        if ((rc = ctx->Uimg[prec].ensure(sap_link_image_bytes(prec, ctx->g, threads)))) return rc;
+        if ((rc = launch_sap_link_image(prec, ctx->g, *U, ctx->Uimg[prec].as<char>(), threads, ctx->stream)))
+            return rc;
+        ctx->Uimg_threads[prec] = threads;
+    }
+    *img = ctx->Uimg[prec].as<char>();
+    return DW_OK;
+}
+
+int sap_check(dw_ctx* ctx) {
+    if (!ctx->sap_err.h || *reinterpret_cast<volatile int*>(ctx->sap_err.h) == 0) return DW_OK;
+    *reinterpret_cast<volatile int*>(ctx->sap_err.h) = 0;
+    return fail(DW_ETIMEOUT, "a SAP domain's bulk copy of its links did not complete");
+}
+
 static int check_prec(int p) { return (p >= 0 && p <= 3) ? DW_OK : fail(DW_EINVAL, "bad precision"); }
 
 }  // namespace dwk
@@ -175,7 +210,8 @@ int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out) {
         return fail(DW_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
     c->sap_threads.assign(4, 0);
-    for (auto* b : {&c->U[0], &c->U[1], &c->U[2], &c->U[3], &c->U[4], &c->work_in, &c->work_out, &c->work_aux})
+    for (auto* b : {&c->U[0], &c->U[1], &c->U[2], &c->U[3], &c->U[4], &c->work_in, &c->work_out, &c->work_aux,
+                   &c->Uimg[0], &c->Uimg[1], &c->Uimg[2], &c->Uimg[3]})
         b->st = c->stream;
     *out = c;
     return DW_OK;
@@ -209,6 +245,7 @@ int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device) {
     }
     if ((rc = launch_gauge_convert(P64, src, ctx->U[P64].as<char>(), ctx->g.V, ctx->stream))) return rc;
     for (int p = 0; p < 5; ++p) ctx->U_ready[p] = false;
+    for (int p = 0; p < 4; ++p) ctx->Uimg_threads[p] = 0;
     ctx->U_ready[P64] = true;
     ctx->have_gauge = true;
     if (ctx->csw != 0.0 && (rc = dw_set_clover(ctx, ctx->csw))) return rc;  // the clover term follows the links
@@ -271,8 +308,8 @@ int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int n
     const long long V = ctx->g.V;
     const long long fb = spinor_bytes(storage, V);
     int rc;
-    const char* U;
-    if ((rc = gauge_for(ctx, storage, &U))) return rc;
+    const char *U, *Uimg;
+    if ((rc = sap_links_for(ctx, storage, ctx->sap_threads[storage], &U, &Uimg))) return rc;
     if ((rc = ctx->work_in.ensure((size_t)nrhs * fb))) return rc;
     if ((rc = ctx->work_out.ensure((size_t)nrhs * fb))) return rc;
     if ((rc = launch_to_internal(storage, v, ctx->work_in.as<char>(), V, nrhs, ctx->stream))) return rc;
@@ -282,13 +319,13 @@ int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int n
             const int mode = (cyc > 0) ? 2 : (colour == 0 ? 0 : 1);
             ProfScope ps(&ctx->prof, "sap_sweep",
                          (double)nrhs * 0.5 * (2.0 * fb + (mode == 2 ? fb : 0) + link_bytes(storage, V)));
-            if ((rc = launch_sap_sweep(storage, storage, ctx->g, ctx->m0, fv, fx, U, nullptr, nrhs, colour, nmr, mode,
-                                       ctx->sap_threads[storage], ctx->stream, ctx->clover())))
+            if ((rc = launch_sap_sweep(storage, storage, ctx->g, ctx->m0, fv, fx, U, Uimg, nullptr, nrhs, colour, nmr,
+                                       mode, ctx->sap_threads[storage], ctx->stream, ctx->clover(), ctx->sap_err.d)))
                 return rc;
         }
     if ((rc = launch_from_internal(storage, ctx->work_out.as<char>(), z, V, nrhs, ctx->stream))) return rc;
     DW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    return DW_OK;
+    return sap_check(ctx);
 }
 
 void dw_default_params(dw_solver_params* P) {

@@ -96,6 +96,15 @@ struct ClovRef {
     const char* a64;
     const char* a32;
 };
+
+// An int in host-mapped pinned memory that kernels set to report a bounded
+// wait that gave up; the host reads it after synchronising the stream.
+struct HostFlag {
+    int* h = nullptr;  // host address
+    int* d = nullptr;  // device address
+    int ensure();
+    ~HostFlag();
+};
 }  // namespace dwk
 
 struct dw_ctx {
@@ -113,6 +122,9 @@ struct dw_ctx {
     double csw = 0.0;               // clover coefficient (0: plain Wilson operator)
     dwk::DevBuf clov64, clov32;     // clover term, FP64 [72][V] and FP32 float4 [18][V]
     dwk::ClovRef clov{nullptr, nullptr};
+    dwk::DevBuf Uimg[4];            // SAP links per domain as shared-memory images (per storage precision)
+    int Uimg_threads[4] = {0, 0, 0, 0};  // CTA size the image was packed for (0: none)
+    dwk::HostFlag sap_err;          // set by a SAP sweep whose link copy did not complete
     const dwk::ClovRef* clover() const { return csw != 0.0 ? &clov : nullptr; }
 };
 
@@ -138,10 +150,21 @@ int launch_clover_compute(const Geom& g, const char* U64, double csw, double* A6
 // One colour half-sweep of SAP (Algorithm 2) on every domain of `colour`:
 // r = v - D x (full operator), nmr MR steps on D^l y = r, x += y.
 // mode 0: x == 0 everywhere (r = v, x = y); 1: x == 0 on this colour; 2: general.
+// Uimg: the links of every domain packed by launch_sap_link_image for the same
+// thread count; err_host: HostFlag::d, set if a link copy did not complete.
 int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
-                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st,
-                     const ClovRef* cl = nullptr);
+                     const char* Uimg, const int* jtab, int nrhs, int colour, int nmr, int mode, int threads,
+                     cudaStream_t st, const ClovRef* cl, int* err_host);
 int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads);
+// CTA size of the SAP sweep (threads, or the domain volume rounded up to a warp multiple when 0)
+int sap_threads(const Geom& g, int threads);
+size_t sap_link_image_bytes(int plink, const Geom& g, int threads);
+int launch_sap_link_image(int plink, const Geom& g, const char* U, char* img, int threads, cudaStream_t st);
+// links of precision prec in both layouts for a sweep of `threads` threads
+// (the image is packed on first use and after dw_set_gauge), and the error flag
+int sap_links_for(dw_ctx* ctx, int prec, int threads, const char** U, const char** img);
+// after the stream was synchronised: DW_ETIMEOUT if a SAP link copy gave up
+int sap_check(dw_ctx* ctx);
 
 // ----- blas.cu -------------------------------------------------------------
 // Outer vectors: flat arrays of 16-byte complex elements, format vp = P64

@@ -27,20 +27,20 @@ namespace {
 //   P64      double2 [4][9][T]                                          (9 x 16 B loads)
 //   P32      float2 [4][9][T]                                           (9 x 8 B loads)
 //   P16/B16  uint4 [4][2][T] (entry quads) + uint32 [4][T] (entry 8)    (2 x 16 B + 4 B)
-// Staging copies each global storage word (component-major [4][9][V]) into
-// its slot with cp.async, so the repacking costs nothing at run time. (FP32
-// entry pairs packed as float4 measured no faster than plain float2 loads.)
+// pack() writes that layout for one site of a domain into a global image of
+// the domain (built once per gauge field), so that a CTA stages all its links
+// with one bulk asynchronous copy. (FP32 entry pairs packed as float4
+// measured no faster than plain float2 loads.)
 template <int PL>
 struct LinkSh;
 template <>
 struct LinkSh<P64> {
     static constexpr int kBytes = 576;
-    static __device__ __forceinline__ void stage(unsigned char* L, int T, int t, const char* U, long long V,
-                                                 long long s) {
+    static __device__ __forceinline__ void pack(unsigned char* L, int T, int t, const char* U, long long V,
+                                                long long s) {
         const double2* Ug = reinterpret_cast<const double2*>(U);
         double2* A = reinterpret_cast<double2*>(L);
-#pragma unroll 4
-        for (int c = 0; c < 36; ++c) cp_async_word(&A[c * T + t], &Ug[(long long)c * V + s]);
+        for (int c = 0; c < 36; ++c) A[c * T + t] = Ug[(long long)c * V + s];
     }
     template <class C>
     static __device__ __forceinline__ void load(const unsigned char* L, int T, int mu, int t, cx<C> u[9]) {
@@ -55,12 +55,11 @@ struct LinkSh<P64> {
 template <>
 struct LinkSh<P32> {
     static constexpr int kBytes = 288;
-    static __device__ __forceinline__ void stage(unsigned char* L, int T, int t, const char* U, long long V,
-                                                 long long s) {
+    static __device__ __forceinline__ void pack(unsigned char* L, int T, int t, const char* U, long long V,
+                                                long long s) {
         const float2* Ug = reinterpret_cast<const float2*>(U);
         float2* A = reinterpret_cast<float2*>(L);
-#pragma unroll 4
-        for (int c = 0; c < 36; ++c) cp_async_word(&A[c * T + t], &Ug[(long long)c * V + s]);
+        for (int c = 0; c < 36; ++c) A[c * T + t] = Ug[(long long)c * V + s];
     }
     template <class C>
     static __device__ __forceinline__ void load(const unsigned char* L, int T, int mu, int t, cx<C> u[9]) {
@@ -75,17 +74,15 @@ struct LinkSh<P32> {
 template <int PL>
 struct LinkSh16 {
     static constexpr int kBytes = 144;
-    static __device__ __forceinline__ void stage(unsigned char* L, int T, int t, const char* U, long long V,
-                                                 long long s) {
+    static __device__ __forceinline__ void pack(unsigned char* L, int T, int t, const char* U, long long V,
+                                                long long s) {
         const uint32_t* Ug = reinterpret_cast<const uint32_t*>(U);
         uint32_t* A = reinterpret_cast<uint32_t*>(L);            // uint4 [4][2][T] seen as words
         uint32_t* B = reinterpret_cast<uint32_t*>(L + 128 * T);  // uint32 [4][T]
-#pragma unroll 2
         for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
             for (int c = 0; c < 8; ++c)
-                cp_async_word(&A[4 * ((mu * 2 + (c >> 2)) * T + t) + (c & 3)], &Ug[(long long)(mu * 9 + c) * V + s]);
-            cp_async_word(&B[mu * T + t], &Ug[(long long)(mu * 9 + 8) * V + s]);
+                A[4 * ((mu * 2 + (c >> 2)) * T + t) + (c & 3)] = Ug[(long long)(mu * 9 + c) * V + s];
+            B[mu * T + t] = Ug[(long long)(mu * 9 + 8) * V + s];
         }
     }
     template <class C>
@@ -172,13 +169,56 @@ __device__ __forceinline__ void block_sum3(C& a, C& b, C& c, C* red) {
     c = sc;
 }
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// mbarrier completed by the byte count of one bulk copy (one arrival)
+__device__ __forceinline__ void bulk_copy_start(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// wait for phase 0 of the mbarrier, giving up after about a second
+__device__ __forceinline__ bool bulk_copy_wait(unsigned long long* bar) {
+    unsigned long long t0 = 0;
+    for (unsigned it = 1;; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar))
+            : "memory");
+        if (done) return true;
+        if ((it & 1023) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > 1000000000ULL)
+                return false;
+        }
+    }
+}
+
 // CLOV: the operator carries the clover term A (site-diagonal, so it is part
 // of D^l on every site): clov is its FP32 storage for float arithmetic and its
-// FP64 storage for double arithmetic.
+// FP64 storage for double arithmetic. Uimg: the links of every domain packed
+// as the shared-memory image of LinkSh<PL> for blockDim.x threads (domain
+// d = D0 + nb0 (D1 + nb1 (D2 + nb2 D3)) at byte d * kBytes * blockDim.x).
+// err_host: set (host-mapped) if the bulk copy of the links did not complete.
 template <int PS, int PL, class C, int MAXT, bool CLOV>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
-    sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref, const char* __restrict__ U, const int* jtab,
-                     int nrhs, int colour, int nmr, int mode, const char* __restrict__ clov) {
+    sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref, const char* __restrict__ U,
+                     const char* __restrict__ Uimg, const int* jtab, int nrhs, int colour, int nmr, int mode,
+                     const char* __restrict__ clov, int* err_host) {
     constexpr int CP = (sizeof(C) == 4) ? P32 : P64;  // storage of the clover term
     typedef LinkSh<PL> LS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -186,6 +226,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     unsigned char* rsh = smem;                                   // rho (MR phase) / own x (residual phase)
     unsigned char* lsh = smem + sizeof(C) * 24 * T;              // links
     C* red = reinterpret_cast<C*>(lsh + (size_t)LS::kBytes * T);  // [32][3]
+    unsigned long long* lbar = reinterpret_cast<unsigned long long*>(red + 96);
 
     const int r = blockIdx.x % nrhs;
     const int e = blockIdx.x / nrhs;
@@ -227,10 +268,14 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
 
     // 1. asynchronous copies global -> shared, all in flight together: the
     //    domain's own links (constant during a solve, so copied before the
-    //    previous sweep has finished) and, once that sweep's x is final, in
-    //    the general mode the domain's own iterate x in storage layout
-    //    (stride T), read by interior hops
-    if (act) LS::stage(lsh, T, tid, U, g.V, s);
+    //    previous sweep has finished; one bulk copy of the domain's image)
+    //    and, once that sweep's x is final, in the general mode the domain's
+    //    own iterate x in storage layout (stride T), read by interior hops
+    if (tid == 0) {
+        const unsigned lbytes = (unsigned)LS::kBytes * (unsigned)T;
+        const long long dom = D[0] + g.nb[0] * (D[1] + g.nb[1] * (D[2] + g.nb[2] * D[3]));
+        bulk_copy_start(lsh, Uimg + dom * lbytes, lbytes, lbar);
+    }
     // every read of v and x and every write of x comes after the previous
     // kernel of the stream has completed (a no-op without a programmatic
     // dependency)
@@ -258,6 +303,14 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     if (act) load_spinor<PS, C>(vb, g.V, s, rho);  // overlaps the copies above
     cp_async_wait();
     __syncthreads();
+    if (__syncthreads_or(!bulk_copy_wait(lbar))) {
+        if (tid == 0) {
+            *reinterpret_cast<volatile int*>(err_host) = 1;
+            __threadfence_system();
+        }
+        bulk_copy_wait(lbar);  // the copy may still be in flight: wait once more before the CTA retires
+        return;
+    }
 
     // 2. residual r = v - D x at this site: interior neighbours and every
     //    forward link from shared memory, boundary neighbours through L2.
@@ -390,11 +443,36 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     }
 }
 
+// the links of domain blockIdx.x (all domains, both colours) in the layout a
+// CTA of blockDim.x threads keeps them in shared memory
+template <int PL>
+__global__ void link_image_kernel(Geom g, const char* __restrict__ U, char* __restrict__ img) {
+    const int t = threadIdx.x;
+    if (t >= g.B) return;
+    int D[4], q = blockIdx.x;
+    D[0] = q % g.nb[0];
+    q /= g.nb[0];
+    D[1] = q % g.nb[1];
+    q /= g.nb[1];
+    D[2] = q % g.nb[2];
+    D[3] = q / g.nb[2];
+    int xg[4], r = t;
+    xg[0] = D[0] * g.b[0] + r % g.b[0];
+    r /= g.b[0];
+    xg[1] = D[1] * g.b[1] + r % g.b[1];
+    r /= g.b[1];
+    xg[2] = D[2] * g.b[2] + r % g.b[2];
+    xg[3] = D[3] * g.b[3] + r / g.b[2];
+    LinkSh<PL>::pack(reinterpret_cast<unsigned char*>(img) + (size_t)blockIdx.x * LinkSh<PL>::kBytes * blockDim.x,
+                     blockDim.x, t, U, g.V, site_index(g, xg));
+}
+
 template <int PS, int PL, class C>
-int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U, const int* jtab, int nrhs,
-                 int colour, int nmr, int mode, int threads, cudaStream_t st, const ClovRef* cl) {
+int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U, const char* Uimg, const int* jtab,
+                 int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st, const ClovRef* cl,
+                 int* err_host) {
     if (cl && threads > 256) return fail(DW_EINVAL, "the clover SAP sweep handles domains of at most 256 sites");
-    const size_t smem = sizeof(C) * 24 * threads + (size_t)LinkSh<PL>::kBytes * threads + sizeof(C) * 3 * 32;
+    const size_t smem = (size_t)sap_smem_bytes(PS, PL, g, threads);
     // the shared-memory limit is a per-device property of the kernel: set it once per device
     static std::mutex mu;
     static std::set<int> done;
@@ -430,14 +508,14 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
     const C diag = (C)(4.0 + m0);
     const char* A = cl ? ((sizeof(C) == 4) ? cl->a32 : cl->a64) : nullptr;
     if (cl)
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, true>, g, diag, v, x, U, jtab, nrhs,
-                                       colour, nmr, mode, A));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, true>, g, diag, v, x, U, Uimg, jtab,
+                                       nrhs, colour, nmr, mode, A, err_host));
     else if (threads <= 256)
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, false>, g, diag, v, x, U, jtab, nrhs,
-                                       colour, nmr, mode, A));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, false>, g, diag, v, x, U, Uimg, jtab,
+                                       nrhs, colour, nmr, mode, A, err_host));
     else
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024, false>, g, diag, v, x, U, jtab, nrhs,
-                                       colour, nmr, mode, A));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024, false>, g, diag, v, x, U, Uimg, jtab,
+                                       nrhs, colour, nmr, mode, A, err_host));
     DW_LAUNCH_CHECK();
     return DW_OK;
 }
@@ -449,25 +527,54 @@ size_t link_sh_bytes(int plink) { return plink == P64 ? 576 : plink == P32 ? 288
 int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads) {
     const size_t c = (pspin == P64) ? 8 : 4;
     (void)g;
-    return (int)(c * 24 * threads + link_sh_bytes(plink) * threads + c * 3 * 32);
+    // rho/x, links, the [32][3] reduction buffer, the links' mbarrier
+    return (int)(c * 24 * threads + link_sh_bytes(plink) * threads + c * 3 * 32 + 16);
+}
+
+int sap_threads(const Geom& g, int threads) { return threads > 0 ? threads : ((g.B + 31) / 32) * 32; }
+
+size_t sap_link_image_bytes(int plink, const Geom& g, int threads) {
+    return link_sh_bytes(plink) * (size_t)sap_threads(g, threads) * (size_t)g.ndom;
+}
+
+int launch_sap_link_image(int plink, const Geom& g, const char* U, char* img, int threads, cudaStream_t st) {
+    threads = sap_threads(g, threads);
+    DW_CUDA_TRY(cudaMemsetAsync(img, 0, sap_link_image_bytes(plink, g, threads), st));  // rows of idle threads
+    const unsigned nb = (unsigned)g.ndom;
+    if (plink == P64)
+        link_image_kernel<P64><<<nb, threads, 0, st>>>(g, U, img);
+    else if (plink == P32)
+        link_image_kernel<P32><<<nb, threads, 0, st>>>(g, U, img);
+    else if (plink == P16)
+        link_image_kernel<P16><<<nb, threads, 0, st>>>(g, U, img);
+    else if (plink == PB16)
+        link_image_kernel<PB16><<<nb, threads, 0, st>>>(g, U, img);
+    else
+        return fail(DW_EINVAL, "unsupported SAP link precision");
+    DW_LAUNCH_CHECK();
+    return DW_OK;
 }
 
 int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
-                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st,
-                     const ClovRef* cl) {
-    if (threads <= 0) threads = ((g.B + 31) / 32) * 32;
+                     const char* Uimg, const int* jtab, int nrhs, int colour, int nmr, int mode, int threads,
+                     cudaStream_t st, const ClovRef* cl, int* err_host) {
+    threads = sap_threads(g, threads);
     if (threads < g.B || threads % 32 != 0 || threads > 1024) return fail(DW_EINVAL, "bad SAP thread count");
     if (sap_smem_bytes(pspin, plink, g, threads) > 227 * 1024)
         return fail(DW_EINVAL, "SAP domain does not fit in shared memory at this precision");
     if (nmr < 1) return fail(DW_EINVAL, "nmr must be >= 1");
     if (pspin == P64 && plink == P64)
-        return sap_launch_t<P64, P64, double>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
+        return sap_launch_t<P64, P64, double>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
+                                            err_host);
     if (pspin == P32 && plink == P32)
-        return sap_launch_t<P32, P32, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
+        return sap_launch_t<P32, P32, float>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
+                                            err_host);
     if (pspin == P16 && plink == P16)
-        return sap_launch_t<P16, P16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
+        return sap_launch_t<P16, P16, float>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
+                                            err_host);
     if (pspin == PB16 && plink == PB16)
-        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, U, jtab, nrhs, colour, nmr, mode, threads, st, cl);
+        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
+                                            err_host);
     return fail(DW_EINVAL, "unsupported SAP precision combination");
 }
 

@@ -79,6 +79,14 @@ size_t request_bytes(const dw_request* q) {
     gauge += dwk::link_bytes(dwk::P32, V);                       // Arnoldi product
     if (half) gauge += dwk::link_bytes(sp, V);
     if (P.outer_prec != DW_F64) gauge += 576 * V;  // double-float links of the residual stencil
+    {  // SAP links packed per domain for the sweep's CTA size
+        long long B = 1, ndom = 1;
+        for (int j = 0; j < 4; ++j) {
+            B *= q->lattice.block[j];
+            ndom *= q->lattice.block[j] > 0 ? q->lattice.dims[j] / q->lattice.block[j] : 0;
+        }
+        gauge += dwk::link_bytes(sp, 1) * ((B + 31) / 32 * 32) * ndom;
+    }
     long long per_rhs = (long long)(P.m + 1) * fv + (long long)P.m * zb + 3 * fb + sb + 24 * 8 * V;
     if (zb != sb) per_rhs += sb;  // SAP output before widening
     if (fv != fb) per_rhs += fv;  // FP32 copy of the residual

@@ -68,7 +68,7 @@ struct Solver {
     long long fv;       // bytes of one basis vector in format vp
     int NP;             // multi-dot row length (m + 2)
     int nblk;
-    const char *U_sap, *U_mv, *U64;
+    const char *U_sap, *U_sap_img, *U_mv, *U64;
     // device buffers (owned by the workspace of the context)
     char *Vb, *Zb, *xb, *bb, *rb, *vlow, *zscr, *rlow, *zsap;
     double2 *partial, *dots, *Qd, *etad;
@@ -127,7 +127,7 @@ struct Solver {
     int start_deflated(int r);
     int sync() {
         DW_CUDA_TRY(cudaStreamSynchronize(st));
-        return DW_OK;
+        return sap_check(ctx);
     }
 };
 
@@ -186,7 +186,9 @@ int Solver::setup() {
     NP = m + 2;
     nblk = blas_nblk(n);
     int rc;
-    if ((rc = gauge_for(ctx, sp, &U_sap))) return rc;
+    if ((rc = sap_links_for(ctx, sp, (ctx->sap_threads.size() > (size_t)sp) ? ctx->sap_threads[sp] : 0, &U_sap,
+                            &U_sap_img)))
+        return rc;
     if ((rc = gauge_for(ctx, mp == P64 ? P64 : P32, &U_mv))) return rc;
     // explicit residual: FP64 links for FP64 outer vectors, double-float links otherwise
     if ((rc = gauge_for(ctx, op == PDF ? PDF : P64, &U64))) return rc;
@@ -473,8 +475,8 @@ int Solver::step() {
             const double bytes = (double)nact * 0.5 * (2.0 * sb + (mode == 2 ? sb : 0) + link_bytes(sp, V));
             ProfScope ps(&ctx->prof, "sap_sweep", bytes);
             const int thr = (ctx->sap_threads.size() > (size_t)sp) ? ctx->sap_threads[sp] : 0;
-            if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zs, U_sap, jtab_d, nrhs, colour, P.mr_steps, mode, thr,
-                                       st, ctx->clover())))
+            if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zs, U_sap, U_sap_img, jtab_d, nrhs, colour, P.mr_steps,
+                                       mode, thr, st, ctx->clover(), ctx->sap_err.d)))
                 return rc;
         }
     if (zp != sp) {

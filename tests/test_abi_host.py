@@ -137,7 +137,8 @@ def test_dense_solve(dw):
 
 @pytest.mark.parametrize("k,outer", [(10, None), (0, None), (10, "f32")])
 def test_request_bytes_formula(dw, k, outer):
-    """Admission estimate: gauge copies (FP64, staging, FP32, FP16, double-float)
+    """Admission estimate: gauge copies (FP64, staging, FP32, FP16, double-float,
+    the 16-bit SAP links packed per domain)
     + per-rhs Krylov workspace (V in the basis format; Z in FP32 when a 16-bit
     SAP is deflated, with the SAP output buffer; x, b, r; SAP input copy;
     canonical staging) + rotation scratch."""
@@ -151,7 +152,7 @@ def test_request_bytes_formula(dw, k, outer):
     sb = 52 * V
     zb = 96 * V if k > 0 else sb
     fv = 96 * V if outer == "f32" else 192 * V
-    gauge = 576 * V + 576 * V + 288 * V + 144 * V + 576 * V
+    gauge = 576 * V + 576 * V + 288 * V + 144 * V + 576 * V + 144 * V  # last: SAP links packed per domain
     per_rhs = 31 * fv + 30 * zb + 3 * 192 * V + sb + 24 * 8 * V
     per_rhs += sb if zb != sb else 0
     per_rhs += fv if outer == "f32" else 0
