@@ -319,7 +319,7 @@ int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int n
             const int mode = (cyc > 0) ? 2 : (colour == 0 ? 0 : 1);
             ProfScope ps(&ctx->prof, "sap_sweep",
                          (double)nrhs * 0.5 * (2.0 * fb + (mode == 2 ? fb : 0) + link_bytes(storage, V)));
-            if ((rc = launch_sap_sweep(storage, storage, ctx->g, ctx->m0, fv, fx, U, Uimg, nullptr, nrhs, colour, nmr,
+            if ((rc = launch_sap_sweep(storage, storage, ctx->g, ctx->m0, fv, fx, Uimg, nullptr, nrhs, colour, nmr,
                                        mode, ctx->sap_threads[storage], ctx->stream, ctx->clover(), ctx->sap_err.d)))
                 return rc;
         }

@@ -369,11 +369,18 @@ __global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, lon
     typedef typename real_of<(PS == P64) ? P64 : P32>::type CL;  // precision of the SAP copy
     const int r = blockIdx.y;
     if (jtab && jtab[r] < 0) return;
+    // 1/||w|| once per CTA: FP64 square root and division are long
+    // instruction sequences on the narrow FP64 pipes
+    __shared__ double inv_sh;
+    if (threadIdx.x == 0) {
+        const double nn = norm2[r];
+        inv_sh = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    }
+    __syncthreads();
+    const double inv = inv_sh;
     const long long s = (long long)blockIdx.x * kT + threadIdx.x;
     if (s >= V) return;
     const int j = jtab ? jtab[r] : 0;
-    const double nn = norm2[r];
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
     const double2* src = w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride;
     double2* out = dst.base + r * dst.rhs_stride + (long long)(j + dst.col_off) * dst.col_stride;
     cx<CL> f[12];
@@ -453,7 +460,10 @@ __global__ void __launch_bounds__(kT) rotate_outer_kernel(double2* X, long long 
     }
 }
 
-// FP32 storage (flat float2 view): X_c = sum_i X_i Q[i][c], in place
+// FP32 storage (flat float2 view): X_c = sum_i X_i Q[i][c], in place; KMAX
+// is the largest kout of the instantiation (it sizes the accumulators); the
+// loads of four inputs are issued together
+template <int KMAX>
 __global__ void __launch_bounds__(kT) rotate_f32_kernel(float2* X, long long rs, long long cs, long long n,
                                                         const int* active, int nin, int kout, const double2* Q,
                                                         int qld) {
@@ -469,13 +479,14 @@ __global__ void __launch_bounds__(kT) rotate_f32_kernel(float2* X, long long rs,
     __syncthreads();
     float2* Xr = X + r * rs;
     for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT) {
-        float ar[kRotMax], ai[kRotMax];
+        float ar[KMAX], ai[KMAX];
 #pragma unroll
-        for (int c = 0; c < kRotMax; ++c) ar[c] = ai[c] = 0.f;
+        for (int c = 0; c < KMAX; ++c) ar[c] = ai[c] = 0.f;
+#pragma unroll 4
         for (int i = 0; i < nin; ++i) {
             const float2 v = Xr[(long long)i * cs + e];
 #pragma unroll
-            for (int c = 0; c < kRotMax; ++c)
+            for (int c = 0; c < KMAX; ++c)
                 if (c < kout) {
                     const float2 qq = q[i * kout + c];
                     ar[c] = fmaf(qq.x, v.x, fmaf(-qq.y, v.y, ar[c]));
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(kT) rotate_f32_kernel(float2* X, long long rs,
                 }
         }
 #pragma unroll
-        for (int c = 0; c < kRotMax; ++c)
+        for (int c = 0; c < KMAX; ++c)
             if (c < kout) Xr[(long long)c * cs + e] = make_float2(ar[c], ai[c]);
     }
 }
@@ -518,6 +529,52 @@ __global__ void __launch_bounds__(kT) rotate_site_kernel(const char* X, char* Y,
             for (int a = 0; a < 12; ++a) acc[a] = acc[a] + qf * v[a];
         }
         store_spinor<P, float>(Y + r * yrs + c * cs, V, s, acc);
+    }
+}
+
+// FP32 Z (float4 [6][V], two complex components per word): one thread per
+// word u = q V + s, i.e. components 2q and 2q + 1 of site s, which are x
+// elements (2q) V + s and (2q + 1) V + s; grid stride; the loads of four Z_i
+// are issued together
+template <int VX>
+__global__ void __launch_bounds__(kT) xupdate_f32_kernel(const float4* Z, long long z_rs, long long z_cs, double2* x,
+                                                         long long x_rs, long long V, const int* nz,
+                                                         const double2* eta, int eta_ld) {
+    typedef Elem<VX> E;
+    typedef typename E::C C;
+    __shared__ C et[kMaxV];
+    const int r = blockIdx.y;
+    const int nv = nz[r];
+    if (nv <= 0) return;
+    for (int i = threadIdx.x; i < nv; i += kT) et[i] = E::from_d2(eta[(long long)r * eta_ld + i]);
+    __syncthreads();
+    const float4* Zr = Z + r * z_rs;
+    double2* xr = x + r * x_rs;
+    const unsigned Vu = (unsigned)V;  // 6 V < 2^31 (contexts hold fewer than 2^31 / 24 sites)
+    for (long long u = (long long)blockIdx.x * kT + threadIdx.x; u < 6 * V; u += (long long)gridDim.x * kT) {
+        const unsigned q = (unsigned)u / Vu;
+        const long long e0 = u + (long long)q * V;  // x element of component 2q
+        C a0 = E::load_rw(xr, e0), a1 = E::load_rw(xr, e0 + V);
+#pragma unroll 4
+        for (int i = 0; i < nv; ++i) {
+            const float4 v = __ldg(&Zr[(long long)i * z_cs + u]);
+            const C h = et[i];
+            if constexpr (VX == PDF) {
+                df_mac_f(a0.re, h.re, v.x);
+                df_mac_f(a0.re, df_neg(h.im), v.y);
+                df_mac_f(a0.im, h.re, v.y);
+                df_mac_f(a0.im, h.im, v.x);
+                df_mac_f(a1.re, h.re, v.z);
+                df_mac_f(a1.re, df_neg(h.im), v.w);
+                df_mac_f(a1.im, h.re, v.w);
+                df_mac_f(a1.im, h.im, v.z);
+            } else {
+                E::mac(a0, h, typename E::C{(double)v.x, (double)v.y});
+                E::mac(a1, h, typename E::C{(double)v.z, (double)v.w});
+            }
+        }
+        E::store(xr, e0, E::fin(a0));
+        E::store(xr, e0 + V, E::fin(a1));
     }
 }
 
@@ -716,8 +773,16 @@ int launch_rotate(int prec, char* X, long long rhs_stride, long long col_stride,
         ROT(kRotMax)
 #undef ROT
     } else if (prec == P32) {
-        rotate_f32_kernel<<<dim3(grid_for(n), nrhs), kT, qsm, st>>>(reinterpret_cast<float2*>(X), rhs_stride / 8,
-                                                                    col_stride / 8, n, active, nin, kout, Q, qld);
+        const dim3 grid(grid_for(n), nrhs);
+        float2* Xf = reinterpret_cast<float2*>(X);
+        if (kout <= 6)
+            rotate_f32_kernel<6><<<grid, kT, qsm, st>>>(Xf, rhs_stride / 8, col_stride / 8, n, active, nin, kout, Q, qld);
+        else if (kout <= 11)
+            rotate_f32_kernel<11><<<grid, kT, qsm, st>>>(Xf, rhs_stride / 8, col_stride / 8, n, active, nin, kout, Q,
+                                                         qld);
+        else
+            rotate_f32_kernel<kRotMax><<<grid, kT, qsm, st>>>(Xf, rhs_stride / 8, col_stride / 8, n, active, nin, kout,
+                                                              Q, qld);
     } else {
         if (!scratch) return fail(DW_EINVAL, "rotation of scaled storage needs scratch");
         const long long yrs = col_stride * kout;
@@ -742,6 +807,16 @@ int launch_xupdate(int prec, int vx, const char* Z, long long z_rs, long long z_
                    long long V, int nrhs, const int* nz, const double2* eta, int eta_ld, cudaStream_t st) {
     dim3 grid((unsigned)((V + kT - 1) / kT), nrhs);
     const long long xrs = x_rs / 16;
+    if (prec == P32 && (vx == PDF || vx == P64)) {  // FP32 Z: one thread per Z word
+        const dim3 eg(grid_for(6 * V), nrhs);
+        const float4* Zf = reinterpret_cast<const float4*>(Z);
+        if (vx == PDF)
+            xupdate_f32_kernel<PDF><<<eg, kT, 0, st>>>(Zf, z_rs / 16, z_cs / 16, x, xrs, V, nz, eta, eta_ld);
+        else
+            xupdate_f32_kernel<P64><<<eg, kT, 0, st>>>(Zf, z_rs / 16, z_cs / 16, x, xrs, V, nz, eta, eta_ld);
+        DW_LAUNCH_CHECK();
+        return DW_OK;
+    }
 #define XUPD(A, B)                                                                                      \
     if (prec == A && vx == B) {                                                                         \
         xupdate_kernel<A, B><<<grid, kT, 0, st>>>(Z, z_rs, z_cs, x, xrs, V, nz, eta, eta_ld);           \

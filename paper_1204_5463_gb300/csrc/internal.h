@@ -151,10 +151,11 @@ int launch_clover_compute(const Geom& g, const char* U64, double csw, double* A6
 // r = v - D x (full operator), nmr MR steps on D^l y = r, x += y.
 // mode 0: x == 0 everywhere (r = v, x = y); 1: x == 0 on this colour; 2: general.
 // Uimg: the links of every domain packed by launch_sap_link_image for the same
-// thread count; err_host: HostFlag::d, set if a link copy did not complete.
-int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
-                     const char* Uimg, const int* jtab, int nrhs, int colour, int nmr, int mode, int threads,
-                     cudaStream_t st, const ClovRef* cl, int* err_host);
+// thread count (the sweep reads its links only there); err_host: HostFlag::d,
+// set if a link copy did not complete.
+int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* Uimg,
+                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st,
+                     const ClovRef* cl, int* err_host);
 int sap_smem_bytes(int pspin, int plink, const Geom& g, int threads);
 // CTA size of the SAP sweep (threads, or the domain volume rounded up to a warp multiple when 0)
 int sap_threads(const Geom& g, int threads);

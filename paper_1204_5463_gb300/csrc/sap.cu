@@ -216,9 +216,8 @@ __device__ __forceinline__ bool bulk_copy_wait(unsigned long long* bar) {
 // err_host: set (host-mapped) if the bulk copy of the links did not complete.
 template <int PS, int PL, class C, int MAXT, bool CLOV>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
-    sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref, const char* __restrict__ U,
-                     const char* __restrict__ Uimg, const int* jtab, int nrhs, int colour, int nmr, int mode,
-                     const char* __restrict__ clov, int* err_host) {
+    sap_sweep_kernel(Geom g, C diag, FieldRef vref, FieldRef xref, const char* __restrict__ Uimg, const int* jtab,
+                     int nrhs, int colour, int nmr, int mode, const char* __restrict__ clov, int* err_host) {
     constexpr int CP = (sizeof(C) == 4) ? P32 : P64;  // storage of the clover term
     typedef LinkSh<PL> LS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -271,11 +270,16 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
     //    previous sweep has finished; one bulk copy of the domain's image)
     //    and, once that sweep's x is final, in the general mode the domain's
     //    own iterate x in storage layout (stride T), read by interior hops
-    if (tid == 0) {
-        const unsigned lbytes = (unsigned)LS::kBytes * (unsigned)T;
-        const long long dom = D[0] + g.nb[0] * (D[1] + g.nb[1] * (D[2] + g.nb[2] * D[3]));
-        bulk_copy_start(lsh, Uimg + dom * lbytes, lbytes, lbar);
-    }
+    const unsigned lbytes = (unsigned)LS::kBytes * (unsigned)T;
+    const int dstride[4] = {1, g.nb[0], g.nb[0] * g.nb[1], g.nb[0] * g.nb[1] * g.nb[2]};
+    const long long dom = D[0] + (long long)dstride[1] * D[1] + (long long)dstride[2] * D[2] +
+                          (long long)dstride[3] * D[3];
+    const unsigned char* limg = reinterpret_cast<const unsigned char*>(Uimg);
+    // the domain one step down in direction mu (periodic)
+    auto dom_lo = [&](int mu) {
+        return D[mu] > 0 ? dom - dstride[mu] : dom + (long long)(g.nb[mu] - 1) * dstride[mu];
+    };
+    if (tid == 0) bulk_copy_start(lsh, limg + dom * lbytes, lbytes, lbar);
     // every read of v and x and every write of x comes after the previous
     // kernel of the stream has completed (a no-op without a programmatic
     // dependency)
@@ -324,8 +328,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             const bool general = (mode == 2);
             const char* xsh = reinterpret_cast<const char*>(rsh);
     // an interior neighbour is read from shared memory and a boundary one
-    // through L2; the branches differ only in the loads, so each direction
-    // runs one hop for the whole warp
+    // through L2 (its link from the neighbouring domain's image, at the
+    // site's index there); the branches differ only in the loads, so each
+    // direction runs one hop for the whole warp
 #define SAP_RES_HOPS(MU, LS_MU)                                                              \
     {                                                                                        \
         const bool inp = lx[MU] + 1 < g.b[MU];                                               \
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
         } else {                                                                             \
             const long long sm = neighbour(g, s, xg, MU, -1);                                \
             load_spinor<PS, C>(xb, g.V, sm, psi);                                            \
-            load_link<PL, C>(U, g.V, MU, sm, u);                                             \
+            LS::template load<C>(limg + dom_lo(MU) * lbytes, T, MU, tid + (g.b[MU] - 1) * LS_MU, u); \
         }                                                                                    \
         if (general || !inm) hop<MU, -1, C, true>(psi, u, acc);                              \
     }
@@ -468,9 +473,8 @@ __global__ void link_image_kernel(Geom g, const char* __restrict__ U, char* __re
 }
 
 template <int PS, int PL, class C>
-int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U, const char* Uimg, const int* jtab,
-                 int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st, const ClovRef* cl,
-                 int* err_host) {
+int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* Uimg, const int* jtab, int nrhs,
+                 int colour, int nmr, int mode, int threads, cudaStream_t st, const ClovRef* cl, int* err_host) {
     if (cl && threads > 256) return fail(DW_EINVAL, "the clover SAP sweep handles domains of at most 256 sites");
     const size_t smem = (size_t)sap_smem_bytes(PS, PL, g, threads);
     // the shared-memory limit is a per-device property of the kernel: set it once per device
@@ -508,14 +512,14 @@ int sap_launch_t(const Geom& g, double m0, FieldRef v, FieldRef x, const char* U
     const C diag = (C)(4.0 + m0);
     const char* A = cl ? ((sizeof(C) == 4) ? cl->a32 : cl->a64) : nullptr;
     if (cl)
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, true>, g, diag, v, x, U, Uimg, jtab,
-                                       nrhs, colour, nmr, mode, A, err_host));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, true>, g, diag, v, x, Uimg, jtab, nrhs,
+                                       colour, nmr, mode, A, err_host));
     else if (threads <= 256)
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, false>, g, diag, v, x, U, Uimg, jtab,
-                                       nrhs, colour, nmr, mode, A, err_host));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 256, false>, g, diag, v, x, Uimg, jtab, nrhs,
+                                       colour, nmr, mode, A, err_host));
     else
-        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024, false>, g, diag, v, x, U, Uimg, jtab,
-                                       nrhs, colour, nmr, mode, A, err_host));
+        DW_CUDA_TRY(cudaLaunchKernelEx(&cfg, sap_sweep_kernel<PS, PL, C, 1024, false>, g, diag, v, x, Uimg, jtab, nrhs,
+                                       colour, nmr, mode, A, err_host));
     DW_LAUNCH_CHECK();
     return DW_OK;
 }
@@ -555,26 +559,26 @@ int launch_sap_link_image(int plink, const Geom& g, const char* U, char* img, in
     return DW_OK;
 }
 
-int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* U,
-                     const char* Uimg, const int* jtab, int nrhs, int colour, int nmr, int mode, int threads,
-                     cudaStream_t st, const ClovRef* cl, int* err_host) {
+int launch_sap_sweep(int pspin, int plink, const Geom& g, double m0, FieldRef v, FieldRef x, const char* Uimg,
+                     const int* jtab, int nrhs, int colour, int nmr, int mode, int threads, cudaStream_t st,
+                     const ClovRef* cl, int* err_host) {
     threads = sap_threads(g, threads);
     if (threads < g.B || threads % 32 != 0 || threads > 1024) return fail(DW_EINVAL, "bad SAP thread count");
     if (sap_smem_bytes(pspin, plink, g, threads) > 227 * 1024)
         return fail(DW_EINVAL, "SAP domain does not fit in shared memory at this precision");
     if (nmr < 1) return fail(DW_EINVAL, "nmr must be >= 1");
     if (pspin == P64 && plink == P64)
-        return sap_launch_t<P64, P64, double>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
-                                            err_host);
+        return sap_launch_t<P64, P64, double>(g, m0, v, x, Uimg, jtab, nrhs, colour, nmr, mode, threads, st,
+                                              cl, err_host);
     if (pspin == P32 && plink == P32)
-        return sap_launch_t<P32, P32, float>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
-                                            err_host);
+        return sap_launch_t<P32, P32, float>(g, m0, v, x, Uimg, jtab, nrhs, colour, nmr, mode, threads, st,
+                                             cl, err_host);
     if (pspin == P16 && plink == P16)
-        return sap_launch_t<P16, P16, float>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
-                                            err_host);
+        return sap_launch_t<P16, P16, float>(g, m0, v, x, Uimg, jtab, nrhs, colour, nmr, mode, threads, st,
+                                             cl, err_host);
     if (pspin == PB16 && plink == PB16)
-        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, U, Uimg, jtab, nrhs, colour, nmr, mode, threads, st, cl,
-                                            err_host);
+        return sap_launch_t<PB16, PB16, float>(g, m0, v, x, Uimg, jtab, nrhs, colour, nmr, mode, threads, st,
+                                               cl, err_host);
     return fail(DW_EINVAL, "unsupported SAP precision combination");
 }
 

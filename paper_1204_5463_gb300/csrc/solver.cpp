@@ -475,7 +475,7 @@ int Solver::step() {
             const double bytes = (double)nact * 0.5 * (2.0 * sb + (mode == 2 ? sb : 0) + link_bytes(sp, V));
             ProfScope ps(&ctx->prof, "sap_sweep", bytes);
             const int thr = (ctx->sap_threads.size() > (size_t)sp) ? ctx->sap_threads[sp] : 0;
-            if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zs, U_sap, U_sap_img, jtab_d, nrhs, colour, P.mr_steps,
+            if ((rc = launch_sap_sweep(sp, sp, g, ctx->m0, Lf, Zs, U_sap_img, jtab_d, nrhs, colour, P.mr_steps,
                                        mode, thr, st, ctx->clover(), ctx->sap_err.d)))
                 return rc;
         }
