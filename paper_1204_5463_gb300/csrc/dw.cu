@@ -158,7 +158,10 @@ constexpr bool clover_combo() {
 template <int PI, int PO, int PL, class C>
 int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const char* U, const int* jtab, int nrhs,
                     const FieldRef* sub, const ClovRef* cl, cudaStream_t st) {
-    const unsigned nb = (unsigned)((g.V + kThreads - 1) / kThreads) * (unsigned)nrhs;
+    // double-float arithmetic holds about 164 registers a thread: 128-thread
+    // blocks let three CTAs (12 warps) share an SM instead of one of 256
+    constexpr int bt = std::is_same<C, df>::value ? 128 : kThreads;
+    const unsigned nb = (unsigned)((g.V + bt - 1) / bt) * (unsigned)nrhs;
     const C diag = C(4.0 + m0);
     FieldRef none{};
     const FieldRef sb = sub ? *sub : none;
@@ -167,11 +170,11 @@ int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const c
             const char* A = (sizeof(C) == 4) ? cl->a32 : cl->a64;
             if (sub) {
                 if constexpr (PO == P64 || PO == PDF)
-                    dw_kernel<PI, PO, PL, C, true, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, A);
+                    dw_kernel<PI, PO, PL, C, true, true><<<nb, bt, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, A);
                 else
                     return fail(DW_EINVAL, "residual stencil requires an FP64-class output");
             } else {
-                dw_kernel<PI, PO, PL, C, false, true><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, A);
+                dw_kernel<PI, PO, PL, C, false, true><<<nb, bt, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, A);
             }
             DW_LAUNCH_CHECK();
             return DW_OK;
@@ -181,11 +184,11 @@ int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const c
     }
     if (sub) {
         if constexpr (PO == P64 || PO == PDF)
-            dw_kernel<PI, PO, PL, C, true, false><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, nullptr);
+            dw_kernel<PI, PO, PL, C, true, false><<<nb, bt, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, nullptr);
         else
             return fail(DW_EINVAL, "residual stencil requires an FP64-class output");
     } else {
-        dw_kernel<PI, PO, PL, C, false, false><<<nb, kThreads, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, nullptr);
+        dw_kernel<PI, PO, PL, C, false, false><<<nb, bt, 0, st>>>(g, diag, in, out, U, jtab, nrhs, sb, nullptr);
     }
     DW_LAUNCH_CHECK();
     return DW_OK;
