@@ -100,8 +100,17 @@ __global__ void __launch_bounds__(kThreads) convert_kernel(FieldRef in, FieldRef
     store_spinor<PO, C>(field_ptr(out, jtab, r), V, s, v);
 }
 
+// CTAs per SM (measured at 24^3 x 48): the FP32 stencil is latency-bound and
+// fastest at three (80 registers), the 16-bit one is issue-bound (decode) and
+// fastest at two (no register cap that forces spills), the Arnoldi product
+// (FP32 in, double-float out) at four; other 16-bit inputs keep three
+template <int PI, int PO, int PL, class C>
+constexpr int dw_min_blocks() {
+    return sizeof(C) != 4 ? 1 : (PI == P32 && PO == P32) ? 3 : (PI == P32) ? 4 : (PO == PI) ? 2 : 3;
+}
+
 template <int PI, int PO, int PL, class C, bool SUB, bool CLOV>
-__global__ void __launch_bounds__(kThreads, (sizeof(C) == 4) ? ((PI == P32) ? 4 : 3) : 1)
+__global__ void __launch_bounds__(kThreads, dw_min_blocks<PI, PO, PL, C>())
     dw_kernel(Geom g, C diag, FieldRef in, FieldRef out, const char* U, const int* jtab, int nrhs, FieldRef sub,
               const char* clov) {
     const int r = blockIdx.x % nrhs;
