@@ -195,8 +195,10 @@ constexpr size_t multidot_smem() {
     return (size_t)kDotStages * (kDotG + 1) * kT * sizeof(typename Elem<VP>::T);
 }
 
-// partial[r][slot][i] over the elements this CTA sweeps, for its group of 8
-// vectors; the CTAs of group 0 also write ||w||^2 and zero the unused slots.
+// partial[r][slot][i] over the elements this CTA sweeps, for its group of at
+// most 8 vectors (the nv vectors of a rhs are spread evenly over the ngroups
+// groups, so that the CTAs of all groups stream about the same bytes); the
+// CTAs of group 0 also write ||w||^2 and zero the unused slots.
 template <int VP>
 __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
                                                          int nv_off, int nvmax, int ngroups, double2* partial) {
@@ -215,8 +217,9 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
     const int slot = blockIdx.x / ngroups;  // partial slot of this CTA
     const int nslots = gridDim.x / ngroups;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int i0 = grp * kDotG;
-    const int G = max(0, min(kDotG, nv - i0));  // vectors of this CTA
+    const int gb = nv / ngroups, gr = nv % ngroups;  // nv <= ngroups * kDotG
+    const int G = gb + (grp < gr ? 1 : 0);           // vectors of this CTA
+    const int i0 = grp * gb + min(grp, gr);
     const TW* Vr = reinterpret_cast<const TW*>(Vb.base + r * Vb.rhs_stride +
                                                (long long)(Vb.col_off + i0) * Vb.col_stride);
     const long long cs = Vb.col_stride * (long long)(16 / sizeof(TW));  // column stride in words
@@ -284,10 +287,7 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
             for (int q = 0; q < kT / 32; ++q) sum += redn[q];
             out[nvmax] = make_double2(sum, 0.0);
         }
-        for (int i = t; i < nvmax; i += kT)
-            if (i >= nv || i >= ngroups * kDotG) out[i] = make_double2(0.0, 0.0);
-    } else if (t >= G && t < kDotG && i0 + t < nvmax) {
-        out[i0 + t] = make_double2(0.0, 0.0);
+        for (int i = nv + t; i < nvmax; i += kT) out[i] = make_double2(0.0, 0.0);  // the groups cover [0, nv)
     }
 }
 
@@ -656,11 +656,17 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
                     int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
     if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
-    // CTAs: (element slots) x (groups of 8 vectors), one wave of two CTAs per
-    // SM per right-hand side; at most nblk slots
+    // CTAs: (element slots) x (groups of at most 8 vectors), at most one wave
+    // of two CTAs per SM per right-hand side (rounded down: a CTA past the
+    // wave would run alone after it); at most nblk slots
     if (nv_active < 1 || nv_active > nvmax) nv_active = nvmax;
     const int ngroups = (nv_active + kDotG - 1) / kDotG;  // groups past every rhs's nv would only read w
-    long long nb = (152LL * 2 + ngroups - 1) / ngroups;
+    static int sms[64] = {0};
+    int dev0 = 0;
+    DW_CUDA_TRY(cudaGetDevice(&dev0));
+    if (dev0 < 64 && sms[dev0] == 0) DW_CUDA_TRY(cudaDeviceGetAttribute(&sms[dev0], cudaDevAttrMultiProcessorCount, dev0));
+    const long long slots = 2LL * ((dev0 < 64 && sms[dev0] > 0) ? sms[dev0] : 152);
+    long long nb = slots / ngroups;
     if (nb > nblk) nb = nblk;
     if (nb > (n + kT - 1) / kT) nb = (n + kT - 1) / kT;
     if (nb < 1) nb = 1;
