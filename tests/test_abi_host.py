@@ -158,3 +158,18 @@ def test_request_bytes_formula(dw, k, outer):
     per_rhs += fv if outer == "f32" else 0
     expect = gauge + 3 * per_rhs + max(k, 1) * zb + (8 << 20)
     assert dw.dw_request_bytes(req) == expect
+
+
+@pytest.mark.parametrize("prec,lb", [("f32", 288), ("f16", 144)])
+def test_request_bytes_ragged_domains(dw, prec, lb):
+    """The per-domain link images are laid out for whole warps: domains of
+    3x2x1x3 = 18 sites are packed for 32-thread CTAs, so the image holds
+    lb * 32 bytes per domain, not lb * 18."""
+    P = dw.dw_default_params(m=20, k=5, nrhs=1, sap_prec=dw.PREC[prec])
+    dims, block = (6, 4, 2, 6), (3, 2, 1, 3)
+    V, ndom = 6 * 4 * 2 * 6, 16
+    # the same request with one 288-site block (not a valid red-black
+    # decomposition: only the estimate is compared) differs in the image term alone
+    other = dw.dw_request_bytes(dw.make_request(dims, (6, 4, 2, 6), -0.3, 1, 1, 1, P))
+    got = dw.dw_request_bytes(dw.make_request(dims, block, -0.3, 1, 1, 1, P))
+    assert got - other == lb * 32 * ndom - lb * 288 * 1
