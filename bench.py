@@ -169,6 +169,30 @@ def dw_bandwidth(peaks, reps=10, dims=(24, 24, 24, 48)):
                      "bytes_per_site": d["bytes"] / d["launches"] / fg.volume(dims),
                      "Gsites_per_s": fg.volume(dims) / avg_s / 1e9,
                      "traffic": kernel_traffic("dw_" + name)}
+    # 12 right-hand sides in one launch: the links count once per site for
+    # all of them (FP32: (288 + 12 x 192) / 12 = 216 B per site and rhs,
+    # FP16: (144 + 12 x 104) / 12 = 116 B); L2 serves the re-reads
+    nb = 12
+    psis = dev(fg.gaussian_source(dims, 8, nrhs=nb))
+    outs = torch.empty_like(psis)
+    for name, prec in (("f32", dw.DW_F32), ("f16", dw.DW_F16)):
+        torch.cuda.nvtx.range_push("dw_apply_batched_" + name)
+        dw.dw_apply(ctx, psis, outs, prec, nb)
+        dw.dw_profile(ctx, True)
+        dw.dw_profile_read(ctx, reset=True)
+        for _ in range(reps):
+            flush.zero_()
+            dw.dw_apply(ctx, psis, outs, prec, nb)
+        torch.cuda.synchronize()
+        d = dw.dw_profile_read(ctx, reset=True)["dw_" + name]
+        dw.dw_profile(ctx, False)
+        torch.cuda.nvtx.range_pop()
+        avg_s = d["total_ms"] / d["launches"] / 1e3
+        gbs = d["bytes"] / d["launches"] / avg_s / 1e9
+        out["batched_12rhs_" + name] = {"GB/s": gbs, "frac": gbs / peaks["hbm_gbs"], "avg_us": avg_s * 1e6,
+                                        "us_per_rhs": avg_s * 1e6 / nb,
+                                        "bytes_per_site_rhs": d["bytes"] / d["launches"] / fg.volume(dims) / nb,
+                                        "Gsites_per_s": nb * fg.volume(dims) / avg_s / 1e9}
     dw.dw_destroy(ctx)
     return out
 

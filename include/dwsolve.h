@@ -101,7 +101,9 @@ int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device);
  * with the clover term, SAP domains are limited to 256 sites. */
 int dw_set_clover(dw_ctx* ctx, double csw);
 
-/* out = D in for nrhs spinor fields (Sec. 1, Eq. "Dw").
+/* out = D in for nrhs spinor fields (Sec. 1, Eq. "Dw"), all in one launch
+ * (the CTAs of one block of sites for the different fields run side by side,
+ * so most re-reads of the links hit L2).
  * in, out: device pointers, canonical FP64 layout, nrhs*V*24 doubles each,
  * non-overlapping. prec selects the storage and arithmetic of the stencil:
  * the input is rounded to prec, D is applied in prec, and the result (in

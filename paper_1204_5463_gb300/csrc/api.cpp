@@ -288,8 +288,12 @@ int dw_apply(dw_ctx* ctx, const double* in, double* out, dw_prec prec, int nrhs)
     if ((rc = ctx->work_out.ensure((size_t)nrhs * fb))) return rc;
     if ((rc = launch_to_internal(prec, in, ctx->work_in.as<char>(), V, nrhs, ctx->stream))) return rc;
     {
+        // algorithmic bytes: every field once, the links once for all
+        // right-hand sides of the launch (its CTAs for one block of sites and
+        // the different rhs run next to each other, so L2 serves the re-reads)
+        const double link_reads = 1.0;
         ProfScope ps(&ctx->prof, prec == DW_F64 ? "dw_f64" : prec == DW_F32 ? "dw_f32" : "dw_f16",
-                     (double)nrhs * (2.0 * fb + link_bytes(prec, V)));
+                     (double)nrhs * 2.0 * fb + link_reads * link_bytes(prec, V));
         FieldRef fi{ctx->work_in.as<char>(), fb, 0, 0}, fo{ctx->work_out.as<char>(), fb, 0, 0};
         if ((rc = launch_dw(prec, prec, prec, ctx->g, ctx->m0, fi, fo, U, nullptr, nrhs, nullptr, ctx->stream,
                             ctx->clover())))

@@ -486,7 +486,10 @@ int Solver::step() {
     // w = D z_j  (written into column j+1 of V)
     {
         const int pl = (mp == P64) ? P64 : P32;
-        ProfScope ps(&ctx->prof, "dw_matvec", (double)nact * ptr_bytes_dw(zp, vp, pl, V));
+        // the links count once for all right-hand sides of the launch (L2 serves the re-reads)
+        const double link_reads = 1.0;
+        ProfScope ps(&ctx->prof, "dw_matvec",
+                     (double)nact * (spinor_bytes(zp, V) + spinor_bytes(vp, V)) + link_reads * link_bytes(pl, V));
         if ((rc = launch_dw(zp, vp, pl, g, ctx->m0, Zf, Vf1, U_mv, jtab_d, nrhs, nullptr, st, ctx->clover())))
             return rc;
     }
