@@ -195,13 +195,43 @@ constexpr size_t multidot_smem() {
     return (size_t)kDotStages * (kDotG + 1) * kT * sizeof(typename Elem<VP>::T);
 }
 
+// The last CTA of a launch (per rhs) to finish sums the partial rows:
+// fin[i] = sum_b part[b][i], each row lane-strided over b and then a fixed
+// shuffle tree, the order of the separate finalize kernel (so the result does
+// not depend on which CTA is last). Every CTA fences its partial writes and
+// counts itself in; the last one reads the rows through L2 and resets the
+// counter for the next launch on the stream.
+__device__ __forceinline__ void last_cta_sum(const double2* part, int nrow, int NP, unsigned* cnt, double2* fin) {
+    __shared__ unsigned is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(cnt, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < NP; i += nw) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int b = lane; b < nrow; b += 32) {
+            const double2 t = __ldcg(part + (long long)b * NP + i);
+            s.x += t.x;
+            s.y += t.y;
+        }
+        s.x = warp_sum(s.x);
+        s.y = warp_sum(s.y);
+        if (lane == 0) fin[i] = s;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+}
+
 // partial[r][slot][i] over the elements this CTA sweeps, for its group of at
 // most 8 vectors (the nv vectors of a rhs are spread evenly over the ngroups
 // groups, so that the CTAs of all groups stream about the same bytes); the
 // CTAs of group 0 also write ||w||^2 and zero the unused slots.
 template <int VP>
 __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
-                                                         int nv_off, int nvmax, int ngroups, double2* partial) {
+                                                         int nv_off, int nvmax, int ngroups, double2* partial,
+                                                         unsigned* cnt, double2* fin) {
     typedef Elem<VP> E;
     typedef typename E::C C;
     typedef typename E::T TW;  // storage word of one complex element
@@ -289,6 +319,7 @@ __global__ void __launch_bounds__(kT, 2) multidot_kernel(VecRef Vb, VecRef w, lo
         }
         for (int i = nv + t; i < nvmax; i += kT) out[i] = make_double2(0.0, 0.0);  // the groups cover [0, nv)
     }
+    if (cnt) last_cta_sum(partial + (long long)r * nslots * NP, nslots, NP, cnt + r, fin + (long long)r * NP);
 }
 
 // out[r][i] = sum_blk partial[r][blk][i]: warp i sums its row lane-strided,
@@ -325,7 +356,8 @@ __global__ void __launch_bounds__(32) finalize_real_kernel(const double2* partia
 // ---- w -= sum_i coef[r][i] V_i ; partial ||w||^2 ------------------------------
 template <int VP>
 __global__ void __launch_bounds__(kT) multiaxpy_kernel(VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off,
-                                                       const double2* coef, int coef_ld, double2* partial) {
+                                                       const double2* coef, int coef_ld, double2* partial,
+                                                       unsigned* cnt, double* fin) {
     typedef Elem<VP> E;
     typedef typename E::C C;
     __shared__ C h[kMaxV];
@@ -357,6 +389,22 @@ __global__ void __launch_bounds__(kT) multiaxpy_kernel(VecRef Vb, VecRef w, long
         double s = 0.0;
         for (int q = 0; q < kT / 32; ++q) s += red[q];
         partial[(long long)r * gridDim.x + blockIdx.x] = make_double2(s, 0.0);
+    }
+    if (cnt) {  // the last CTA sums the partial norms in the finalize kernel's order
+        __shared__ unsigned is_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) is_last = (atomicAdd(cnt + r, 1u) == gridDim.x - 1);
+        __syncthreads();
+        if (!is_last || threadIdx.x >= 32) return;
+        __threadfence();
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(&partial[(long long)r * gridDim.x + b].x);
+        s = warp_sum(s);
+        if (threadIdx.x == 0) {
+            fin[r] = s;
+            cnt[r] = 0u;
+        }
     }
 }
 
@@ -653,7 +701,7 @@ bool basis_ok(int vp) { return vp == P64 || vp == PDF || vp == P32; }
 int blas_nblk(long long n) { return (int)grid_for(n); }
 
 int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nv_active,
-                    int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st) {
+                    int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st, unsigned* cnt) {
     if (nvmax > kMaxV) return fail(DW_EINVAL, "too many basis vectors for one multi-dot");
     if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
     // CTAs: (element slots) x (groups of at most 8 vectors), at most one wave
@@ -689,30 +737,40 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
         }
     }
     if (vp == PDF)
-        multidot_kernel<PDF><<<grid, kT, multidot_smem<PDF>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+        multidot_kernel<PDF><<<grid, kT, multidot_smem<PDF>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial,
+                                                                    cnt, out);
     else if (vp == P32)
-        multidot_kernel<P32><<<grid, kT, multidot_smem<P32>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+        multidot_kernel<P32><<<grid, kT, multidot_smem<P32>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial,
+                                                                    cnt, out);
     else
-        multidot_kernel<P64><<<grid, kT, multidot_smem<P64>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial);
+        multidot_kernel<P64><<<grid, kT, multidot_smem<P64>(), st>>>(Vb, w, n, jtab, nv_off, nvmax, ngroups, partial,
+                                                                    cnt, out);
     DW_LAUNCH_CHECK();
-    finalize_kernel<<<nrhs, 1024, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
-    DW_LAUNCH_CHECK();
+    if (!cnt) {  // without counters, a separate reduction launch
+        finalize_kernel<<<nrhs, 1024, 0, st>>>(partial, (int)nb, nvmax + 1, jtab, out);
+        DW_LAUNCH_CHECK();
+    }
     return DW_OK;
 }
 
 int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs,
                      const double2* coef, int coef_ld, double2* partial, int nblk, double* out_norm2,
-                     cudaStream_t st) {
+                     cudaStream_t st, unsigned* cnt) {
     if (!basis_ok(vp)) return fail(DW_EINVAL, "bad basis precision");
     if (vp == PDF)
-        multiaxpy_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
+        multiaxpy_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial, cnt,
+                                                              out_norm2);
     else if (vp == P32)
-        multiaxpy_kernel<P32><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
+        multiaxpy_kernel<P32><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial, cnt,
+                                                              out_norm2);
     else
-        multiaxpy_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial);
+        multiaxpy_kernel<P64><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial, cnt,
+                                                              out_norm2);
     DW_LAUNCH_CHECK();
-    finalize_real_kernel<<<nrhs, 32, 0, st>>>(partial, nblk, jtab, out_norm2);
-    DW_LAUNCH_CHECK();
+    if (!cnt) {
+        finalize_real_kernel<<<nrhs, 32, 0, st>>>(partial, nblk, jtab, out_norm2);
+        DW_LAUNCH_CHECK();
+    }
     return DW_OK;
 }
 

@@ -180,12 +180,14 @@ struct VecRef {
 // out[r][i] = <V_i, w>  (i < nv[r]),  out[r][nvmax] = ||w||^2 ; nv = jtab[r] + nv_off (or nv_off)
 // nv_active: the largest number of basis vectors any rhs has in this launch
 // (sizes the grid); nvmax: the row length of partial/out minus one
+// cnt: nrhs zeroed counters (left zeroed): the last CTA of each rhs sums the
+// partial rows itself; nullptr: a separate reduction launch
 int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nvmax, int nv_active,
-                    int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st);
+                    int nrhs, double2* partial, int nblk, double2* out, cudaStream_t st, unsigned* cnt = nullptr);
 // w -= sum_i coef[r][i] V_i (i < nv[r]);  out_norm2[r] = ||w||^2 after the update
 int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, int nv_off, int nrhs,
                      const double2* coef, int coef_ld, double2* partial, int nblk, double* out_norm2,
-                     cudaStream_t st);
+                     cudaStream_t st, unsigned* cnt = nullptr);
 // dst = w / sqrt(norm2[r]) per site; if plow >= 0 also written to `low` in spinor storage plow
 int launch_normalize(int vp, VecRef w, VecRef dst, long long V, const int* jtab, int nrhs, const double* norm2,
                      int plow, FieldRef low, cudaStream_t st);

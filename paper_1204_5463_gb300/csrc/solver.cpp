@@ -72,6 +72,7 @@ struct Solver {
     // device buffers (owned by the workspace of the context)
     char *Vb, *Zb, *xb, *bb, *rb, *vlow, *zscr, *rlow, *zsap;
     double2 *partial, *dots, *Qd, *etad;
+    unsigned* cnt_d;  // reduction counters of the multi-dot and multi-axpy launches
     double *norm2d, *scal_d;
     int *jtab_d, *nz_d;
     // pinned host mirrors
@@ -135,7 +136,7 @@ struct Solver {
 
 // Workspace kept by the context between solves (grown on demand).
 struct Workspace {
-    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, norm2, scal, jtab, nz, canon;
+    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, norm2, scal, jtab, nz, canon, cnt;
     double2* dots_h = nullptr;
     double* norm2_h = nullptr;
     int* jtab_h = nullptr;
@@ -159,7 +160,8 @@ static Workspace* workspace_of(dw_ctx* ctx) {
         if (ctx->ws)
             for (DevBuf* b : {&ctx->ws->V, &ctx->ws->Z, &ctx->ws->x, &ctx->ws->b, &ctx->ws->r, &ctx->ws->vlow,
                               &ctx->ws->zscr, &ctx->ws->rlow, &ctx->ws->zsap, &ctx->ws->partial, &ctx->ws->dots, &ctx->ws->Q, &ctx->ws->eta,
-                              &ctx->ws->norm2, &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon})
+                              &ctx->ws->norm2, &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon,
+                              &ctx->ws->cnt})
                 b->st = ctx->stream;
     }
     return ctx->ws;
@@ -204,6 +206,10 @@ int Solver::setup() {
     if (vp != op && (rc = W->rlow.ensure((size_t)nrhs * fv))) return rc;
     if ((rc = W->zscr.ensure((size_t)(k > 0 ? k : 1) * zb))) return rc;
     if ((rc = W->partial.ensure((size_t)nrhs * nblk * NP * sizeof(double2)))) return rc;
+    // per-rhs counters of the multi-dot and multi-axpy launches (their last CTA
+    // reduces the partial sums and leaves the counter at zero); zeroed per solve
+    if ((rc = W->cnt.ensure((size_t)nrhs * sizeof(unsigned)))) return rc;
+    DW_CUDA_TRY(cudaMemsetAsync(W->cnt.p, 0, (size_t)nrhs * sizeof(unsigned), st));
     if ((rc = W->dots.ensure((size_t)2 * nrhs * NP * sizeof(double2)))) return rc;
     if ((rc = W->Q.ensure((size_t)(m + 1) * (m + 1) * sizeof(double2)))) return rc;
     if ((rc = W->eta.ensure((size_t)(m + 1) * sizeof(double2)))) return rc;
@@ -239,6 +245,7 @@ int Solver::setup() {
     zsap = (zp != sp) ? W->zsap.as<char>() : nullptr;
     rlow = (vp != op) ? W->rlow.as<char>() : nullptr;
     partial = W->partial.as<double2>();
+    cnt_d = W->cnt.as<unsigned>();
     dots = W->dots.as<double2>();
     Qd = W->Q.as<double2>();
     etad = W->eta.as<double2>();
@@ -311,7 +318,7 @@ int Solver::start_deflated(int r) {
     {
         ProfScope ps(&ctx->prof, "multidot", (double)(mm + 2) * fv);
         if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, mm + 1, m + 1, mm + 1, 1, partial,
-                                  nblk, dots, st)))
+                                  nblk, dots, st, cnt_d)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * NP, cudaMemcpyDeviceToHost, st));
@@ -362,10 +369,11 @@ int Solver::start_deflated(int r) {
     for (int pass = 0; pass < 2; ++pass) {
         ProfScope ps(&ctx->prof, "cgs", (double)(2 * k + 3) * fv);
         VecRef w = vref_all(r, k);
-        if ((rc = launch_multidot(vp, vref_all(r, 0), w, n, nullptr, k, m + 1, k, 1, partial, nblk, dots, st)))
+        if ((rc = launch_multidot(vp, vref_all(r, 0), w, n, nullptr, k, m + 1, k, 1, partial, nblk, dots, st,
+                                  cnt_d)))
             return rc;
         if ((rc = launch_multiaxpy(vp, vref_all(r, 0), w, n, nullptr, k, 1, dots, NP, partial, nblk, norm2d + r,
-                                   st)))
+                                   st, cnt_d)))
             return rc;
     }
     {
@@ -378,7 +386,7 @@ int Solver::start_deflated(int r) {
     {
         ProfScope ps(&ctx->prof, "multidot", (double)(k1 + 1) * fv);
         if ((rc = launch_multidot(vp, vref_all(r, 0), res_vec(r), n, nullptr, k1, m + 1, k1, 1, partial, nblk, dots,
-                                  st)))
+                                  st, cnt_d)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * NP, cudaMemcpyDeviceToHost, st));
@@ -503,13 +511,13 @@ int Solver::step() {
     {
         ProfScope ps(&ctx->prof, "cgs_project", (jsum + nact) * fv);
         if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, jmax + 1, nrhs, partial,
-                                  nblk, dots, st)))
+                                  nblk, dots, st, cnt_d)))
             return rc;
     }
     {
         ProfScope ps(&ctx->prof, "cgs_update", (jsum + 2.0 * nact) * fv);
         if ((rc = launch_multiaxpy(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial, nblk,
-                                   norm2d, st)))
+                                   norm2d, st, cnt_d)))
             return rc;
     }
     DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
@@ -543,10 +551,10 @@ int Solver::step() {
         {
             ProfScope ps(&ctx->prof, "cgs_reorth", (2.0 * js2 + 3.0 * n2) * fv);
             if ((rc = launch_multidot(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, m + 1, jmax2 + 1, nrhs,
-                                      partial, nblk, dots, st)))
+                                      partial, nblk, dots, st, cnt_d)))
                 return rc;
             if ((rc = launch_multiaxpy(vp, vref_all(0, 0), vref_all(0, 1), n, jtab_d, 1, nrhs, dots, NP, partial,
-                                       nblk, norm2d, st)))
+                                       nblk, norm2d, st, cnt_d)))
                 return rc;
         }
         DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
