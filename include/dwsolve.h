@@ -118,7 +118,10 @@ int dw_apply(dw_ctx* ctx, const double* in, double* out, dw_prec prec, int nrhs)
  * and adds x^l += y^l. storage selects the precision of v, x and the links
  * (arithmetic FP32 for DW_F32/F16/BF16, FP64 for DW_F64).
  * v, z: device pointers, canonical FP64 layout, nrhs fields each.
- * Requires ncycles >= 1, nmr >= 1. */
+ * Requires ncycles >= 1, nmr >= 1. Each domain's CTA waits (at most about a
+ * second) for the bulk copy of its links; if a wait gives up the call, and a
+ * solve whose preconditioner it was, returns DW_ETIMEOUT.
+ * Errors: DW_EINVAL, DW_ENOMEM, DW_ECUDA, DW_ETIMEOUT. */
 int sap_precondition(dw_ctx* ctx, const double* v, double* z, int ncycles, int nmr, dw_prec storage, int nrhs);
 
 typedef struct {
@@ -171,7 +174,9 @@ void dw_default_params(dw_solver_params* P);
  * ||r_explicit|| / ||r_implicit|| > clean_restart_t.
  * b, x: canonical FP64 layout, nrhs fields, device pointers unless
  * P->host_buffers. Returns DW_OK when every rhs met tol, DW_ENOTCONV when a
- * limit stopped the solve (x then holds the last iterate), or an error code.
+ * limit stopped the solve (x then holds the last iterate), or an error code
+ * (DW_EINVAL, DW_ENOMEM, DW_ECUDA, DW_EBREAKDOWN, DW_ENONFINITE, and
+ * DW_ETIMEOUT when a SAP sweep's bounded wait for its links gave up).
  * S may be NULL. */
 int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S);
 
