@@ -481,7 +481,7 @@ def main():
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serving-outer", default="df64", choices=["df64", "f32"],
-                    help="Arnoldi basis of the served solves (f32: the single-precision scheme of Sec. 4.7)")
+                    help="Arnoldi basis of the served solves (f32: the single-precision scheme of Sec. 5.7)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="wilson_16x16x16x32 (default, the benchmark line), batched_24x24x24x48, mixed_32x32x32x64, "
                          "sap_standalone (SAP as a solver around the spectral edge, 16^3x32)")
@@ -630,7 +630,7 @@ def main():
         mb = {"value": mb_value, "unit": "solves/s", "nrhs": 12, "sap_prec": "f16", "steps": nb_steps,
               "ms_per_step": mms / nb_steps, "iterations_max": S12.iterations,
               "true_rel_res_max": max(S12.true_rel_res[i] for i in range(12)), "ratio_vs_plain": mb_value / value}
-        # the same with the single-precision Arnoldi basis of Sec. 4.7 (refined per cycle)
+        # the same with the single-precision Arnoldi basis of Sec. 5.7 (refined per cycle)
         P12s = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
                                     mr_steps=cfg["mr_steps"], sap_prec=dw.DW_F16, matvec_prec=dw.DW_F32, nrhs=12,
                                     outer_prec=dw.DW_F32)

@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the CUDA path, the CPU oracle and the tests.
 
 This module holds no arithmetic of the solver itself: it only draws the
-objects the method operates on (Sec. 1 of the paper defines them):
+objects the method operates on (Sec. 2 of the paper defines them):
 
 * a gauge field ``U[site][mu][row][col]`` of SU(3) link matrices,
 * right-hand sides ``b[site][spin][colour]`` (Gaussian or point sources),

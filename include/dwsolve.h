@@ -2,7 +2,7 @@
  * dwsolve.h -- C ABI of the GB300 library for the Wilson-Dirac system D x = b
  * solved by SAP-preconditioned flexible GMRES with deflated restarts.
  *
- * Operator (Sec. 1, Eq. "Dw" of Frommer, Nobile, Zingler, arXiv:1204.5463),
+ * Operator (Sec. 2, Eq. "Dw" of Frommer, Nobile, Zingler, arXiv:1204.5463),
  * written with a bare mass m0:
  *     (D psi)_n = (4 + m0) psi_n
  *                 - 1/2 sum_{j=1..4} [ (1 + gamma_j) U_{n,j} psi_{n+j}
@@ -58,10 +58,10 @@ extern "C" {
  *           vectors of fgmresdr_solve (outer_prec). */
 typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3, DW_DF64 = 4 } dw_prec;
 
-/* Lattice L = {0 <= n <= d-1} (Sec. 1) and its decomposition into domains
+/* Lattice L = {0 <= n <= d-1} (Sec. 2) and its decomposition into domains
  * L^l of block[] sites each. Requirements: dims[j] >= 2; block[j] >= 1;
  * dims[j] % block[j] == 0 and dims[j] / block[j] even (red-black colouring
- * without same-colour coupling, Sec. 1 / Fig. 1); block volume <= 1024. */
+ * without same-colour coupling, Sec. 2 / Fig. 1); block volume <= 1024. */
 typedef struct {
     int dims[4];
     int block[4];
@@ -86,7 +86,7 @@ int dw_set_mass(dw_ctx* ctx, double m0);
  * internal storage precisions on first use; the caller's buffer is not kept. */
 int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device);
 
-/* Add the clover term of the improved operators of Sec. 5 (the paper cites
+/* Add the clover term of the improved operators of Sec. 6 (the paper cites
  * the Sheikholeslami-Wohlert term without a formula; this is the standard
  * site-diagonal form):
  *   D_sw = D + A,  A_n = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}(n),
@@ -101,7 +101,7 @@ int dw_set_gauge(dw_ctx* ctx, const double* U, int on_device);
  * with the clover term, SAP domains are limited to 256 sites. */
 int dw_set_clover(dw_ctx* ctx, double csw);
 
-/* out = D in for nrhs spinor fields (Sec. 1, Eq. "Dw"), all in one launch
+/* out = D in for nrhs spinor fields (Sec. 2, Eq. "Dw"), all in one launch
  * (the CTAs of one block of sites for the different fields run side by side,
  * so most re-reads of the links hit L2).
  * in, out: device pointers, canonical FP64 layout, nrhs*V*24 doubles each,
@@ -110,11 +110,11 @@ int dw_set_clover(dw_ctx* ctx, double csw);
  * prec storage) is widened back to FP64. 1 <= nrhs <= DW_MAX_RHS. */
 int dw_apply(dw_ctx* ctx, const double* in, double* out, dw_prec prec, int nrhs);
 
-/* z = M v with M the SAP preconditioner (Sec. 3): ncycles iterations of
+/* z = M v with M the SAP preconditioner (Sec. 4): ncycles iterations of
  * Algorithm 2 started from x = 0, each a sweep over the domains of colour 0
  * (block coordinates summing to an even number; contains site 0) followed by
  * colour 1. Each domain solve computes r = (v - D x)^l with the full
- * operator, runs nmr minimal-residual steps on D^l y = r from y = 0 (Sec. 3)
+ * operator, runs nmr minimal-residual steps on D^l y = r from y = 0 (Sec. 4)
  * and adds x^l += y^l. storage selects the precision of v, x and the links
  * (arithmetic FP32 for DW_F32/F16/BF16, FP64 for DW_F64).
  * v, z: device pointers, canonical FP64 layout, nrhs fields each.
@@ -135,13 +135,13 @@ typedef struct {
     int mr_steps;           /* MR steps per domain solve                                   */
     dw_prec sap_prec;       /* storage precision of SAP fields and of the Z basis          */
     dw_prec matvec_prec;    /* precision of the Arnoldi product w = D z (DW_F64 or DW_F32) */
-    double clean_restart_t; /* clean restart when ||r_explicit|| / ||r_implicit|| > t (Sec. 4.7) */
+    double clean_restart_t; /* clean restart when ||r_explicit|| / ||r_implicit|| > t (Sec. 5.7) */
     int nrhs;               /* right-hand sides solved together, 1..DW_MAX_RHS             */
     int host_buffers;       /* 1: b and x are host pointers (copies inside the call)       */
     int use_x0;             /* 1: x holds the initial guess; 0: x0 = 0                     */
     dw_prec outer_prec;     /* outer vectors and their Gram-Schmidt / update arithmetic:
                                DW_F64 (V, x, b, r in FP64), DW_DF64 (default: double-float),
-                               or DW_F32: the single-precision Arnoldi process of Sec. 4.7
+                               or DW_F32: the single-precision Arnoldi process of Sec. 5.7
                                (V and all basis arithmetic in FP32, x, b, r and the
                                explicit residual double-float; needs sap_prec F32/F16/BF16
                                and matvec_prec DW_F32)                                      */
@@ -166,9 +166,9 @@ void dw_default_params(dw_solver_params* P);
 /* Solve D x = b for nrhs right-hand sides with FGMRES-DR (Algorithm 4):
  * flexible Arnoldi (Algorithm 3) with classical Gram-Schmidt and selective
  * reorthogonalisation in the basis precision (outer_prec), Givens-updated
- * implicit residual (Sec. 4.2, 4.6),
+ * implicit residual (Sec. 5.2, 5.6),
  * harmonic Ritz deflation (Lemma 1a, Eqs. "G_kplus1", "hatHk"), and the
- * refinement scheme of Sec. 4.7 (Algorithm 5): every cycle recomputes r = b - D x in FP64 and
+ * refinement scheme of Sec. 5.7 (Algorithm 5): every cycle recomputes r = b - D x in FP64 and
  * injects it into the least-squares right-hand side, the last column of
  * G_{k+1} and v_{k+1}; a clean restart follows when
  * ||r_explicit|| / ||r_implicit|| > clean_restart_t.
@@ -206,7 +206,7 @@ int dw_profile_read(dw_ctx* ctx, dw_kernel_stat* out, int max, int* n, int reset
  * Chooses the SAP domain block for a lattice by the time to solution of a
  * calibration solve per candidate (the block changes the preconditioner, so
  * iteration counts change with it). Candidates: block[j] divides dims[j] with
- * dims[j] / block[j] even (red-black colouring, Sec. 1), 32..1024 sites per
+ * dims[j] / block[j] even (red-black colouring, Sec. 2), 32..1024 sites per
  * domain, aspect ratio <= 2, SAP shared memory within one CTA; the twelve
  * closest to 256 sites per domain (most isotropic first) are timed.
  * L: dims and m0 (block ignored); U: device canonical FP64 gauge field;

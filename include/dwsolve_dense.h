@@ -30,8 +30,8 @@ int dw_dense_qr(int rows, int cols, const double* G, double* Q, double* R);
 /* Least squares min || c - H eta || for a rows x cols H (rows >= cols + 1)
  * whose first dense_rows - 1 columns may be full in rows 0..dense_rows-1 and
  * whose later columns j have nonzeros in rows 0..j+1 (the matrix of a
- * deflated cycle, Sec. 4.5; dense_rows = 1 gives plain upper Hessenberg), by
- * Givens rotations added column by column (Sec. 4.2, 4.6).
+ * deflated cycle, Sec. 5.5; dense_rows = 1 gives plain upper Hessenberg), by
+ * Givens rotations added column by column (Sec. 5.2, 5.6).
  * eta: cols complex; residual[j] = least-squares residual norm using columns
  * 0..j (the implicit residual after step j). */
 int dw_dense_lstsq(int rows, int cols, int dense_rows, const double* H, const double* c, double* eta,

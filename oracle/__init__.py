@@ -8,19 +8,19 @@ library (``paper_1204_5463_gb300``) and never imports it.
 Pieces and the passages they follow (Frommer, Nobile, Zingler, "Deflation and
 Flexible SAP-Preconditioning of GMRES in Lattice QCD Simulation"):
 
-* ``dw``, ``dw_local`` -- Eq. "Dw" and Eq. "Dw_local" (Sec. 1), in C
+* ``dw``, ``dw_local`` -- Eq. "Dw" and Eq. "Dw_local" (Sec. 2), in C
   (``dw_oracle.c``), mass form ``D = (4+m0) - 1/2 H_hop = D_kappa/(2 kappa)``.
 * ``sap`` -- Algorithm 2 (SAP iteration) with minimal-residual local solves
-  (Sec. 3), in C.
+  (Sec. 4), in C.
 * ``clover`` -- the site-diagonal clover term of the improved operators of
-  Sec. 5 (a reading: the paper cites it without a formula), in C; ``dw``,
+  Sec. 6 (a reading: the paper cites it without a formula), in C; ``dw``,
   ``dw_local`` and ``sap`` add it when given.
 * ``flexible_arnoldi`` -- Algorithm 3 (flexible Arnoldi, modified Gram-Schmidt
   as printed).
 * ``fgmresdr`` -- Algorithm 4 (F-GMRES-DR) with the harmonic Ritz extraction of
   Lemma 1a, the deflated restart of Eqs. "G_kplus1", "tildeV_Vplus1", "hatHk",
-  and the explicit-residual injection and clean restart of Sec. 4.7. ``k = 0``
-  gives restarted FGMRES (Sec. 4.2-4.3).
+  and the explicit-residual injection and clean restart of Sec. 5.7. ``k = 0``
+  gives restarted FGMRES (Sec. 5.2-5.3).
 * ``tune_m0`` -- the bare mass that puts the smallest |eigenvalue| of D at a
   chosen distance from the origin, from Arnoldi (ARPACK) on D at m0 = 0 and the
   identity spec(D_m0) = spec(D_0) + m0.
@@ -248,11 +248,11 @@ def deflated_restart(V, Z, H, mm: int, k: int, r):
 
     * harmonic Ritz pairs of Lemma 1a, the k of smallest modulus -> G_k,
     * G_{k+1} = [[G_k, g], [0, gamma]] with [g; gamma] = V_{m+1}^H r (the
-      explicit residual in the old basis, Sec. 4.7), QR with real positive
+      explicit residual in the old basis, Sec. 5.7), QR with real positive
       diag(R),
     * Hhat_k = Q_{k+1}^H Hhat Q_k (Eq. "hatHk"), V_{k+1} = V_{m+1} Q_{k+1},
       Z_k = Z_m Q_k (Eq. "tildeV_Vplus1"),
-    * v_{k+1} := r orthonormalised against V_k (Sec. 4.7),
+    * v_{k+1} := r orthonormalised against V_k (Sec. 5.7),
     * c = [V_{k+1}^H r].
 
     Returns (V_{k+1} rows, Z_k rows, Hhat_k, c, selected Ritz values).
@@ -292,7 +292,7 @@ class SolveResult:
 
 def fgmresdr(A, M, b, m: int, k: int, tol: float, max_cycles: int = 1000, t_clean: float = 4.0,
              x0=None, max_iterations: int | None = None, on_cycle=None) -> SolveResult:
-    """Algorithm 4 (F-GMRES-DR) with the refinement scheme of Sec. 4.7 (Algorithm 5).
+    """Algorithm 4 (F-GMRES-DR) with the refinement scheme of Sec. 5.7 (Algorithm 5).
 
     Readings taken (the paper leaves these open):
 
@@ -303,7 +303,7 @@ def fgmresdr(A, M, b, m: int, k: int, tol: float, max_cycles: int = 1000, t_clea
     * a cycle ends early once the least-squares (implicit) residual is
       ``<= tol ||b||``; then the explicit check decides.
     * the explicitly recomputed residual r replaces the updated one in three
-      places (Sec. 4.7): the last column of G_{k+1} is V_{m+1}^H r, the
+      places (Sec. 5.7): the last column of G_{k+1} is V_{m+1}^H r, the
       vector v_{k+1} is r orthonormalised (two classical Gram-Schmidt passes)
       against V_k = V_{m+1} Q_k, and c = [V_{k+1}^H r; 0].
     * the QR factorisation of G_{k+1} is the one with a real positive

@@ -11,23 +11,23 @@
  *   spinor       psi[site][spin 0..3][colour 0..2]          (12 complex / site)
  *   gauge field  U[site][mu 0..3][row 0..2][col 0..2]        (36 complex / site)
  *
- * Operator (Sec. 1, Eq. "Dw"), written with a bare mass m0 instead of kappa:
+ * Operator (Sec. 2, Eq. "Dw"), written with a bare mass m0 instead of kappa:
  *   (D psi)_n = (4+m0) psi_n
  *               - 1/2 sum_j [ (1+gamma_j) U_{n,j} psi_{n+j}
  *                            + (1-gamma_j) U^dagger_{n-j,j} psi_{n-j} ]
  * which equals D_kappa / (2 kappa) with kappa = 1/(2(4+m0)); n +- j is taken
  * modulo d_j (periodic in all four directions).
  *
- * Local operator (Sec. 1, Eq. "Dw_local"): the same sum restricted to hops
+ * Local operator (Sec. 2, Eq. "Dw_local"): the same sum restricted to hops
  * whose both ends lie in the same domain L^l (a 4-D box of block[] sites).
  *
- * SAP (Sec. 1, Algorithm 2): domains are coloured by the parity of the sum of
+ * SAP (Sec. 2, Algorithm 2): domains are coloured by the parity of the sum of
  * their block coordinates; colour 0 (the one containing site 0) is swept first.
  * Each sweep computes r^l = (b - D x)^l with the full operator, approximately
  * solves D^l y^l = r^l, and adds the correction: x^l <- x^l + y^l.
  *
  * Clover term (the Sheikholeslami-Wohlert improvement of the operators in
- * Sec. 5; the paper cites it without a formula, so this is a reading): a
+ * Sec. 6; the paper cites it without a formula, so this is a reading): a
  * site-diagonal 12x12 matrix added to D and to every D^l,
  *   A_n = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(n),
  *   sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu],
@@ -35,11 +35,11 @@
  * with Q the sum of the four plaquettes in the (mu, nu) plane that start and
  * end at n, all traversed in the same sense (mu first, then nu).
  *
- * Local solver (Sec. 3): nmr steps of minimal residual (MR) from y = 0:
+ * Local solver (Sec. 4): nmr steps of minimal residual (MR) from y = 0:
  *   p = D^l rho;  alpha = <p,rho>/<p,p>  (<a,b> = a^H b);  y += alpha rho;
  *   rho -= alpha p.  nmr == 0 selects an exact solve by Gaussian elimination
  *   with partial pivoting (small domains only), used to pin SAP against the
- *   closed series form of the preconditioner (Sec. 3).
+ *   closed series form of the preconditioner (Sec. 4).
  */
 #include <complex.h>
 #include <math.h>

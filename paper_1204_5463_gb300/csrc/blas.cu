@@ -79,7 +79,7 @@ struct Elem<P64> {
     static __device__ __forceinline__ C add(C a, C b) { return C{a.re + b.re, a.im + b.im}; }
 };
 
-// FP32 basis vectors (the single-precision Arnoldi process of Sec. 4.7): one
+// FP32 basis vectors (the single-precision Arnoldi process of Sec. 5.7): one
 // float2 per complex element, in the S32 spinor layout (float4[6][V], two
 // complex per site and plane). Dot products and updates are element-wise, so
 // they never depend on which complex element sits where; the per-site

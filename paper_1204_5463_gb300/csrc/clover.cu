@@ -1,5 +1,5 @@
 // Clover term of the improved Wilson operator (the Sheikholeslami-Wohlert
-// term of the operators in Sec. 5; the paper cites it without a formula):
+// term of the operators in Sec. 6; the paper cites it without a formula):
 //   A_n = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(n),
 //   F_{mu nu}(n) = (Q - Q^dagger)/8 made traceless, Q = sum of the four
 //   plaquettes in the (mu, nu) plane that start and end at n (same sense),

@@ -1,7 +1,7 @@
 // Device-side building blocks shared by the CUDA kernels of the library:
 // complex arithmetic, storage formats of spinor and link fields, lattice
 // geometry, and the spin-projected hopping term of the Wilson-Dirac operator
-// (Sec. 1, Eq. "Dw").
+// (Sec. 2, Eq. "Dw").
 #pragma once
 
 #include <cuda_bf16.h>

@@ -1,7 +1,7 @@
 // Small dense complex FP64 linear algebra for the outer FGMRES-DR loop
 // (host side; matrices are at most (m+1) x m with m <= 63):
 //   * Givens-updated QR of the (generalised) Hessenberg matrix giving the
-//     implicit residual norm and the least-squares coefficients (Sec. 4.2, 4.6),
+//     implicit residual norm and the least-squares coefficients (Sec. 5.2, 5.6),
 //   * LU solve with partial pivoting (for H_m^H f_m = h_m, Lemma 1a),
 //   * the complex eigenproblem of H_m + f_m h_m^H (Lemma 1a): Householder
 //     reduction to Hessenberg form, shifted QR iteration to Schur form,

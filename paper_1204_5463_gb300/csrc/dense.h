@@ -8,7 +8,7 @@ namespace dwk {
 
 typedef std::complex<double> zd;
 
-// QR of a growing least-squares matrix by Givens rotations (Sec. 4.2, 4.6):
+// QR of a growing least-squares matrix by Givens rotations (Sec. 5.2, 5.6):
 // columns are added one at a time; the leading block of a deflated cycle may
 // be full (non-Hessenberg), later columns have one subdiagonal entry.
 // residual() = || c - Hhat eta || for the least-squares eta of the columns so far.

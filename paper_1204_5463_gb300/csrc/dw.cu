@@ -1,4 +1,4 @@
-// Wilson-Dirac stencil D (Sec. 1, Eq. "Dw") on the full periodic lattice, and
+// Wilson-Dirac stencil D (Sec. 2, Eq. "Dw") on the full periodic lattice, and
 // the layout conversions between the canonical FP64 layout of the C ABI and
 // the component-major device layouts (common.cuh).
 //

@@ -1,5 +1,5 @@
-// One colour half-sweep of the Schwarz alternating procedure (Sec. 1,
-// Algorithm 2) with inexact minimal-residual domain solves (Sec. 3).
+// One colour half-sweep of the Schwarz alternating procedure (Sec. 2,
+// Algorithm 2) with inexact minimal-residual domain solves (Sec. 4).
 //
 // One CTA owns one domain L^l of the swept colour (and one right-hand side);
 // one thread owns one site of the domain. The CTA

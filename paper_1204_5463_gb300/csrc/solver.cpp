@@ -4,18 +4,18 @@
 // per-rhs column table): preconditioning z_j = M v_j (SAP sweeps), the
 // Arnoldi product w = D z_j, classical Gram-Schmidt with selective
 // reorthogonalisation, normalisation. Host side: the (m+1) x m Hessenberg
-// matrix per rhs, its Givens QR (implicit residual, Sec. 4.2 and 4.6), and at each
+// matrix per rhs, its Givens QR (implicit residual, Sec. 5.2 and 5.6), and at each
 // cycle end the least-squares solve, the harmonic Ritz eigenproblem
 // (Lemma 1a) and the QR of G_{k+1} (Eq. "G_kplus1").
 //
-// Refinement scheme of Sec. 4.7 (Algorithm 5): every cycle ends with an explicit FP64
+// Refinement scheme of Sec. 5.7 (Algorithm 5): every cycle ends with an explicit FP64
 // residual r = b - D x. It supplies the last column of G_{k+1} (V_{m+1}^H r),
 // the vector v_{k+1} (r orthonormalised against V_k) and the right-hand side
 // c = [V_{k+1}^H r; 0]; a clean restart (plain first cycle from r) follows
 // when ||r|| / ||r_implicit|| > t.
 //
 // The Arnoldi basis V is kept either in the format of x, b, r (FP64 or
-// double-float) or, as in the single-precision scheme of Sec. 4.7, in FP32
+// double-float) or, as in the single-precision scheme of Sec. 5.7, in FP32
 // (outer_prec = DW_F32): then the whole Arnoldi process, the deflated restart
 // and the least-squares right-hand side run on FP32 vectors, while x, b and
 // the explicit residual stay double-float, so every cycle refines the

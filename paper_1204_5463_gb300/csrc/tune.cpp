@@ -2,7 +2,7 @@
 // so the iteration count) as well as the cost of a sweep, so candidates are
 // ranked by the time to solution of a calibration solve, not by sweep time.
 // Candidates: b_j divides d_j with d_j / b_j even (red-black colouring,
-// Sec. 1), block volume within [32, 1024] sites, aspect ratio <= 2, SAP
+// Sec. 2), block volume within [32, 1024] sites, aspect ratio <= 2, SAP
 // shared memory within the per-CTA limit; the twelve closest to 256 sites are
 // timed. Results are cached per lattice, right-hand-side count, precisions and
 // solver parameters.

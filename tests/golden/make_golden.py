@@ -8,7 +8,7 @@ Every value in these files comes from ``oracle/`` (and the seeded inputs of
 tiny_4x4x4x4_fgmresdr.json — the tiny workload (4^4 lattice, eps 0.3, seed 0,
 m0 = -0.5, 2^4 domains, SAP 4 cycles x 4 MR steps, FGMRES-DR m = 20, k = 5,
 tol 1e-10, Gaussian right-hand side seed 1), solved by the oracle's
-Algorithm 4 with the refinement of Sec. 4.7: Arnoldi steps, cycles, clean
+Algorithm 4 with the refinement of Sec. 5.7: Arnoldi steps, cycles, clean
 restarts, the per-cycle (steps, implicit, explicit) relative residuals, the
 harmonic Ritz values kept at each deflated restart (Lemma 1a), the norm of
 the solution and its first components; and D = Eq. "Dw" applied to the
@@ -43,7 +43,7 @@ def main():
     Db = oracle.dw(U, b, dims, cfg["m0"])
     out = {
         "workload": "tiny_4x4x4x4",
-        "source": "oracle (FP64 CPU): Algorithm 4 with the refinement of Sec. 4.7; Eq. \"Dw\"",
+        "source": "oracle (FP64 CPU): Algorithm 4 with the refinement of Sec. 5.7; Eq. \"Dw\"",
         "config": {"dims": list(dims), "block": list(cfg["block"]), "eps": cfg["eps"], "seed": cfg["seed"],
                    "m0": cfg["m0"], "sap_cycles": cfg["sap_cycles"], "mr_steps": cfg["mr_steps"], "m": cfg["m"],
                    "k": cfg["k"], "tol": cfg["tol"], "rhs_seed": 1},

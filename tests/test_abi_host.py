@@ -2,7 +2,7 @@
 
 * the shared library loads and exports every function that include/*.h declares;
 * the small dense FP64 routines of the outer loop (eigenproblem of Lemma 1a,
-  QR of G_{k+1}, Givens least squares of Sec. 4.2 and 4.6, LU solve) agree with
+  QR of G_{k+1}, Givens least squares of Sec. 5.2 and 5.6, LU solve) agree with
   numpy.linalg on random matrices.
 """
 

@@ -1,5 +1,5 @@
 """GPU test of the domain-tile autotuner: every candidate obeys the
-red-black constraint of Sec. 1, the winner is the fastest converged
+red-black constraint of Sec. 2, the winner is the fastest converged
 candidate, solving with it meets the tolerance, and the choice is cached."""
 
 import numpy as np

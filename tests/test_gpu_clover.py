@@ -1,5 +1,5 @@
 """GPU parity of the clover-improved operator (the site-diagonal term of the
-operators of Sec. 5) against the FP64 oracle: the clover field computed on
+operators of Sec. 6) against the FP64 oracle: the clover field computed on
 the device enters D, the SAP sweeps and the solver exactly as the oracle's
 A does. Tolerances as for the plain operator."""
 

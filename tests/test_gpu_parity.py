@@ -187,7 +187,7 @@ def test_fgmresdr_low_precision_sap_converges(dw, sap_prec):
 
 @pytest.mark.parametrize("sap_prec", [1, 2])
 def test_fgmresdr_fp32_basis_converges(dw, sap_prec):
-    """Single-precision Arnoldi process with double-float refinement (Sec. 4.7):
+    """Single-precision Arnoldi process with double-float refinement (Sec. 5.7):
     the FP32 basis still reaches the 1e-10 true residual (checked with the
     oracle's D), within cond*tol of the oracle solution, in a comparable number
     of Arnoldi steps."""

@@ -3,7 +3,7 @@
 Every check here is independent of the oracle's own formulas: closed forms
 (free-field plane waves), symmetries (gamma5-hermiticity, gauge covariance),
 dense linear algebra on tiny lattices (numpy LU / eig), the series form of the
-SAP preconditioner (Sec. 3) and the invariants of the Krylov layer (Eqs.
+SAP preconditioner (Sec. 4) and the invariants of the Krylov layer (Eqs.
 "arnoldilike", "harmRitz", "hatHk", "r").
 """
 
@@ -170,7 +170,7 @@ def test_local_operator_is_principal_submatrix():
     sd = np.repeat(dom, 12)
     same = sd[:, None] == sd[None, :]
     assert np.abs(Al - np.where(same, A, 0)).max() < 1e-14
-    # the colouring: no coupling between distinct domains of the same colour (Sec. 1)
+    # the colouring: no coupling between distinct domains of the same colour (Sec. 2)
     sc = np.repeat(col, 12)
     cross_same_colour = (sc[:, None] == sc[None, :]) & ~same
     assert np.abs(A[cross_same_colour]).max() == 0.0
@@ -182,7 +182,7 @@ def test_local_operator_is_principal_submatrix():
 def test_sap_exact_local_solves_equal_series(s):
     """SAP with exact domain solves, s cycles from 0, equals
     M = sum_{j<s} (A_L^{-1} A_U)^j A_L^{-1} of the red-black block splitting
-    (Sec. 3; colour 0 is the leading block, swept first)."""
+    (Sec. 4; colour 0 is the leading block, swept first)."""
     dims, block, m0 = (4, 4, 4, 2), (2, 2, 2, 1), -0.5
     U = fg.gauge_field(dims, 0.3, seed=0)
     V = fg.volume(dims)
@@ -356,7 +356,7 @@ def test_residuals_monotone_and_consistent():
 
 
 def test_deflation_reduces_iterations_near_critical():
-    """Sec. 5: at fixed m, deflation needs fewer matrix-vector products, most
+    """Sec. 6: at fixed m, deflation needs fewer matrix-vector products, most
     visibly near the critical mass."""
     dims, block = (4, 4, 2, 2), (2, 2, 1, 1)
     U = fg.gauge_field(dims, 0.5, seed=0)
@@ -460,7 +460,7 @@ def test_clover_operator_gamma5_hermitian_and_local_submatrix():
 
 
 def test_clover_sap_exact_local_solves_equal_series():
-    """The series form of SAP (Sec. 3) holds for the clover-improved operator."""
+    """The series form of SAP (Sec. 4) holds for the clover-improved operator."""
     dims, block, m0 = (4, 4, 4, 2), (2, 2, 2, 1), -0.5
     U = fg.gauge_field(dims, 0.3, seed=0)
     V = fg.volume(dims)
