@@ -21,9 +21,13 @@ Flexible SAP-Preconditioning of GMRES in Lattice QCD Simulation"):
   Lemma 1a, the deflated restart of Eqs. "G_kplus1", "tildeV_Vplus1", "hatHk",
   and the explicit-residual injection and clean restart of Sec. 5.7. ``k = 0``
   gives restarted FGMRES (Sec. 5.2-5.3).
-* ``tune_m0`` -- the bare mass that puts the smallest |eigenvalue| of D at a
-  chosen distance from the origin, from Arnoldi (ARPACK) on D at m0 = 0 and the
-  identity spec(D_m0) = spec(D_0) + m0.
+* ``tune_m0_schur``, ``tune_m0_arnoldi``, ``tune_m0`` -- the bare mass that
+  puts the leftmost eigenvalue of D at a chosen real part delta, from the
+  identity spec(D_m0) = spec(D_0) + m0 and the leftmost Ritz value of D_0
+  (thick-restarted Arnoldi ``krylov_schur_edge``, a single Arnoldi process
+  ``arnoldi_ritz``, or ARPACK), each with the residual norm of its Ritz pair.
+  Not from the paper, which quotes kappa values of thermalised fields: these
+  set up the synthetic workloads near the critical mass of Sec. 6.
 
 Small dense steps use numpy.linalg library routines (lstsq, qr, eig, solve).
 Readings where the paper is silent are stated next to the code that takes them.
@@ -424,10 +428,13 @@ def solve(U, b, dims, block, m0, sap_cycles, mr_steps, m, k, tol, clov=None, **k
     return fgmresdr(A, M, np.asarray(b).reshape(-1), m, k, tol, **kw)
 
 
-def arnoldi_ritz(apply, n: int, m: int, seed: int = 0):
+def arnoldi_ritz(apply, n: int, m: int, seed: int = 0, return_vectors: bool = False):
     """Ritz values of an m-step Arnoldi process (classical Gram-Schmidt with one
     reorthogonalisation) started from a seeded random vector, with their
-    residual bounds |h_{m+1,m} e_m^T y|. Exterior eigenvalues converge first."""
+    residual norms |h_{m+1,m} e_m^T y| (y the unit eigenvector of H_m), which
+    equal ||A x - theta x|| for the unit Ritz vector x = V_m y. Exterior
+    eigenvalues converge first. With return_vectors the Ritz vectors are
+    returned too, as the columns of an n x m array."""
     rng = np.random.default_rng(seed)
     V = np.zeros((m + 1, n), dtype=np.complex128)
     H = np.zeros((m + 1, m), dtype=np.complex128)
@@ -443,16 +450,25 @@ def arnoldi_ritz(apply, n: int, m: int, seed: int = 0):
         V[j + 1] = w / H[j + 1, j]
     theta, Y = np.linalg.eig(H[:m, :m])
     bounds = np.abs(H[m, m - 1] * Y[m - 1, :])
+    if return_vectors:
+        return theta, bounds, V[:m].T @ Y
     return theta, bounds
 
 
 def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int = 40, tol: float = 1e-3,
-                      seed: int = 0):
+                      seed: int = 0, return_vector: bool = False, log=None):
     """Leftmost eigenvalue estimate by thick-restarted Arnoldi (Krylov-Schur,
-    Stewart 2002) in bounded memory: m-dimensional bases, restarted on the k
-    Schur vectors of smallest real part, until the leftmost Ritz value's
-    residual bound |h_{m+1,m} z_{m,1}| is below tol. Returns (theta, bound,
-    matvecs)."""
+    Stewart 2002) in bounded memory.
+
+    Each restart expands the basis to m vectors, takes the Ritz pairs of the
+    m x m block H_m and the residual norm of each, |h_{m+1,m} e_m^T y| with y
+    the unit eigenvector of H_m (it equals ||A x - theta x|| for the unit Ritz
+    vector x = V_m y), stops once the leftmost Ritz value's residual is below
+    tol, and otherwise keeps the k Schur vectors of H_m whose Ritz values have
+    the smallest real parts (a Schur form ordered so that they lead). Returns
+    (theta, residual norm, matvecs), plus the unit Ritz vector with
+    return_vector. log, when given, is called with (restart, matvecs, theta,
+    residual) after every restart."""
     import scipy.linalg as sla
 
     rng = np.random.default_rng(seed)
@@ -462,8 +478,8 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
     V[0] = v / np.linalg.norm(v)
     p = 0
     matvecs = 0
-    theta = bound = None
-    for _ in range(max_restarts):
+    theta = bound = y = None
+    for restart in range(max_restarts):
         for j in range(p, m):
             w = np.asarray(apply(V[j]), dtype=np.complex128)
             matvecs += 1
@@ -473,17 +489,19 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
                 H[:j + 1, j] += h
             H[j + 1, j] = np.linalg.norm(w)
             V[j + 1] = w / H[j + 1, j]
-        lam = np.linalg.eigvals(H[:m, :m])
+        # Ritz pairs of H_m and their residual norms (from the eigenvectors)
+        lam, Y = np.linalg.eig(H[:m, :m])
+        res = np.abs(H[m, m - 1]) * np.abs(Y[m - 1, :]) / np.linalg.norm(Y, axis=0)
+        i = int(np.argmin(lam.real))
+        theta, bound, y = lam[i], float(res[i]), Y[:, i] / np.linalg.norm(Y[:, i])
+        if log is not None:
+            log(restart, matvecs, theta, bound)
+        if bound < tol or restart == max_restarts - 1:
+            break
+        # thick restart on the Schur vectors of the k leftmost Ritz values
         cut = np.sort(lam.real)[k - 1]
         T, Z, sdim = sla.schur(H[:m, :m], output="complex", sort=lambda x: x.real <= cut)
         kk = max(1, min(sdim, m - 1))
-        ritz = np.diagonal(T)[:kk]
-        bounds = np.abs(H[m, m - 1] * Z[m - 1, :kk])
-        i = int(np.argmin(ritz.real))
-        theta, bound = ritz[i], bounds[i]
-        if bound < tol:
-            break
-        # truncate to the selected Schur vectors and restart
         Vk = Z[:, :kk].T @ V[:m]
         hrow = H[m, m - 1] * Z[m - 1, :kk]
         vlast = V[m].copy()
@@ -494,17 +512,21 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
         H[:kk, :kk] = T[:kk, :kk]
         H[kk, :kk] = hrow
         p = kk
+    if return_vector:
+        return theta, bound, matvecs, V[:m].T @ y
     return theta, bound, matvecs
 
 
-def tune_m0_schur(U, dims, target: float, m: int = 60, k: int = 20, tol: float = 1e-3, seed: int = 0, clov=None):
-    """As tune_m0_arnoldi with a thick-restarted Arnoldi (bounded memory)."""
+def tune_m0_schur(U, dims, target: float, m: int = 60, k: int = 20, tol: float = 1e-3, seed: int = 0, clov=None,
+                  max_restarts: int = 40, log=None):
+    """As tune_m0_arnoldi with a thick-restarted Arnoldi (bounded memory).
+    Returns (m0, theta*, its residual norm, matvecs, seconds)."""
     V = int(np.prod(dims))
     U = _cvec(U)
     t0 = time.time()
     theta, bound, mv = krylov_schur_edge(
-        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0, A=clov).reshape(-1), 12 * V, m, k, tol=tol,
-        seed=seed)
+        lambda v: dw(U, np.asarray(v).reshape(V, 4, 3), dims, 0.0, A=clov).reshape(-1), 12 * V, m, k,
+        max_restarts=max_restarts, tol=tol, seed=seed, log=log)
     return target - theta.real, theta, bound, mv, time.time() - t0
 
 

@@ -378,6 +378,104 @@ def test_tune_m0_places_smallest_eigenvalue():
     assert abs(ev.real.min() - 1e-2) < 1e-6
 
 
+def _leftmost(ev, theta):
+    """The eigenvalue of smallest real part nearest theta (the leftmost
+    eigenvalues of a gamma5-hermitian D come in conjugate pairs)."""
+    edge = ev[np.abs(ev.real - ev.real.min()) < 1e-9]
+    return edge[np.argmin(np.abs(edge - theta))]
+
+
+def test_arnoldi_ritz_full_space_reproduces_dense_spectrum():
+    """With as many steps as the dimension, the Arnoldi Ritz values are the
+    eigenvalues of D (dense numpy eig)."""
+    dims = (2, 2, 2, 2)
+    U = fg.gauge_field(dims, 0.5, seed=3)
+    A = _dense(U, dims, 0.0)
+    n = A.shape[0]
+    theta, _ = oracle.arnoldi_ritz(lambda v: A @ v, n, n, seed=1)
+    ev = np.linalg.eigvals(A)
+    # every eigenvalue is matched by a Ritz value and vice versa
+    assert max(np.abs(ev - t).min() for t in theta) < 1e-8
+    assert max(np.abs(theta - e).min() for e in ev) < 1e-8
+
+
+def test_arnoldi_ritz_residual_norms_are_true_residuals():
+    """The reported residual of every Ritz pair equals ||D x - theta x|| of the
+    returned unit Ritz vector, and bounds the distance of theta to the spectrum
+    of D in the sense sigma_min(D - theta) <= residual (theta is an exact
+    eigenvalue of a perturbation of D of that norm)."""
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.5, seed=0)
+    A = _dense(U, dims, 0.0)
+    n = A.shape[0]
+    theta, bounds, X = oracle.arnoldi_ritz(lambda v: A @ v, n, 60, seed=2, return_vectors=True)
+    for i in np.argsort(theta.real)[:6]:
+        x = X[:, i]
+        assert abs(np.linalg.norm(x) - 1.0) < 1e-10
+        true = np.linalg.norm(A @ x - theta[i] * x)
+        assert abs(true - bounds[i]) <= 1e-9 + 1e-7 * true
+        smin = np.linalg.svd(A - theta[i] * np.eye(n), compute_uv=False)[-1]
+        assert smin <= bounds[i] * (1 + 1e-8) + 1e-12
+
+
+def test_krylov_schur_edge_converges_to_leftmost_eigenvalue():
+    """Thick-restarted Arnoldi on a 768-dimensional D (several restarts) finds
+    the eigenvalue of smallest real part of the dense spectrum, with a residual
+    norm below the tolerance that is the true residual of its Ritz vector."""
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.5, seed=0)
+    A = _dense(U, dims, 0.0)
+    n = A.shape[0]
+    seen = []
+    theta, bound, mv, x = oracle.krylov_schur_edge(lambda v: A @ v, n, m=40, k=12, max_restarts=400, tol=1e-9,
+                                                  seed=4, return_vector=True, log=lambda *a: seen.append(a))
+    assert mv > 40 and len(seen) > 1              # it did restart
+    ev = np.linalg.eigvals(A)
+    assert abs(theta.real - ev.real.min()) < 1e-7
+    assert abs(theta - _leftmost(ev, theta)) < 1e-7
+    assert bound < 1e-9
+    assert abs(np.linalg.norm(A @ x - theta * x) - bound) < 1e-10
+
+
+def test_krylov_schur_reported_residual_is_the_ritz_vectors_at_every_restart():
+    """Stopped early (loose tolerance), the returned residual is still the true
+    residual of the returned Ritz pair, not that of a Schur vector."""
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.6, seed=1)
+    A = _dense(U, dims, 0.0)
+    n = A.shape[0]
+    for restarts in (1, 2, 5):
+        theta, bound, mv, x = oracle.krylov_schur_edge(lambda v: A @ v, n, m=30, k=10, max_restarts=restarts,
+                                                      tol=0.0, seed=5, return_vector=True)
+        true = np.linalg.norm(A @ x - theta * x)
+        assert abs(true - bound) <= 1e-10 + 1e-7 * true
+        smin = np.linalg.svd(A - theta * np.eye(n), compute_uv=False)[-1]
+        assert smin <= bound * (1 + 1e-8) + 1e-12
+
+
+@pytest.mark.parametrize("how", ["schur", "arnoldi"])
+def test_tuned_mass_puts_dense_spectrum_edge_at_target(how):
+    """m0 = target - Re(theta*) shifts the leftmost eigenvalue of D_{m0}
+    (dense eig) to real part target: a sign error in the shift, or an edge
+    taken from the wrong Ritz value, moves it by at least the spread of the
+    low spectrum."""
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.5, seed=0)
+    target = 1e-2
+    if how == "schur":
+        m0, theta, bound, _, _ = oracle.tune_m0_schur(U, dims, target, m=40, k=12, tol=1e-9, max_restarts=400, seed=4)
+    else:
+        m0, theta, bound, _ = oracle.tune_m0_arnoldi(U, dims, target, m=12 * fg.volume(dims), seed=4)
+    ev = np.linalg.eigvals(_dense(U, dims, m0))
+    assert bound < 1e-8
+    assert abs(ev.real.min() - target) < 1e-7
+    assert abs(_leftmost(ev, target + 1j * theta.imag) - (target + 1j * theta.imag)) < 1e-7
+    # every eigenvalue has real part >= target, so min |lambda| >= target (on
+    # this small lattice an eigenvalue right of the edge but nearer the real
+    # axis is the smallest in modulus)
+    assert np.abs(ev).min() >= target - 1e-9
+
+
 # --------------------------------------------------------------------------- clover term
 def _abelian_field(dims, b):
     """U_{n,0} = diag(e^{i b n_1}, e^{-i b n_1}, 1), all other links 1: a uniform
