@@ -243,12 +243,20 @@ int dw_autotune_block(const dw_lattice* L, const double* U, const double* b, con
  * (V*72 doubles); in, out: device pointers, one canonical FP64 spinor field
  * each (V*24 doubles); cuda_stream: cudaStream_t or NULL. Returns after the
  * work on the stream has completed.
- * The first call on a device looks up the array's device address (set-up, once
- * per device); make that first call before any stream capture. Every call
- * overwrites the whole part of the array it reads, so nothing needs clearing,
- * but all calls share the array: calls that overlap on the GPU (other threads
- * or streams) race and must be serialised by the caller. Every GPU that loads
- * the library holds the 2 MiB until the process exits. */
+ * Set-up: the first call on each device is the set-up step. Under CUDA's
+ * default lazy module loading that call is what loads the library's device
+ * code on the device and so places the 2 MiB array there (the driver does this,
+ * not the library), and it looks up the array's device address with
+ * cudaGetSymbolAddress, once per device, with that device current. Make the
+ * first call outside stream capture and before entering any region in which
+ * the process must not allocate (or set CUDA_MODULE_LOADING=EAGER so the
+ * array is placed when the context is created). From then on the device holds
+ * the 2 MiB until the process exits, and calls allocate nothing. The cached
+ * address belongs to the device's current primary context: do not use this
+ * entry point after cudaDeviceReset on that device.
+ * Every call overwrites the whole part of the array it reads, so nothing needs
+ * clearing, but all calls share the array: calls that overlap on the GPU
+ * (other threads or streams) race and must be serialised by the caller. */
 int dw_apply_f32_noalloc(const int* dims, double m0, const double* U, const double* in, double* out,
                          void* cuda_stream);
 

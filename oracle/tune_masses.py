@@ -1,12 +1,14 @@
 """Writes fieldgen/spectral_edges.json: the left spectral edge of D (at m0 = 0)
 for every synthetic gauge field the workloads use, from the oracle only.
 
-The edge is the Ritz value of smallest real part of an m-step Arnoldi process
-on the oracle's D (oracle.tune_m0_arnoldi). Since spec(D_m0) = spec(D_0) + m0,
-a workload that wants its smallest |eigenvalue| near delta takes
-m0 = delta - Re(edge) (fieldgen.lattice_configs does this).
+The edge is the leftmost Ritz value of a thick-restarted Arnoldi process
+(Krylov-Schur, ``oracle.tune_m0_schur``) on the oracle's D, run until the
+residual norm of its Ritz pair is at most ``tol``. Since
+spec(D_m0) = spec(D_0) + m0, a workload that wants the leftmost eigenvalue of
+D at real part delta takes m0 = delta - Re(edge) (fieldgen.lattice_configs
+does this); ``tol`` is a tenth of the smallest delta the field is used with.
 
-Usage: python -m oracle.tune_masses [--only NAME]
+Usage: python -m oracle.tune_masses [--only KEY] [--max-matvecs N]
 """
 
 from __future__ import annotations
@@ -25,59 +27,63 @@ import oracle  # noqa: E402
 
 OUT = os.path.join(ROOT, "fieldgen", "spectral_edges.json")
 
-# (dims, eps, seed, Arnoldi steps); 0 steps selects the thick-restarted
-# (Krylov-Schur) variant, which keeps 61 basis vectors for the 32^3 x 64 field.
+# (dims, eps, seed, c_sw, residual tolerance), cheapest first. The tolerance is
+# a tenth of the smallest delta the field serves: 1e-2 for the 16^3 x 32 bench
+# and clover workloads, 5e-3 for the batched 24^3 x 48 one, 1e-3 for the mixed
+# 32^3 x 64 one and for the served requests (delta in [1e-3, 1e-2]).
 FIELDS = [
-    ((16, 16, 16, 32), 0.5, 0, 200),
-    ((24, 24, 24, 48), 0.5, 0, 200),
-    ((32, 32, 32, 64), 0.6, 0, 0),
-] + [((8, 8, 8, 16), e, 0, 200) for e in (0.3, 0.45, 0.6)] \
-  + [((16, 16, 16, 32), e, 0, 200) for e in (0.3, 0.45, 0.6)] \
-  + [((24, 24, 24, 48), e, 0, 160) for e in (0.3, 0.45, 0.6)]
-
-
-# clover-improved operators: (dims, eps, seed, Arnoldi steps, c_sw)
-CLOVER_FIELDS = [((16, 16, 16, 32), 0.5, 0, 0, 1.91)]
-
-
-def key(dims, eps, seed, csw=0.0):
-    k = f"{'x'.join(map(str, dims))}_eps{eps}_seed{seed}"
-    return k + (f"_csw{csw}" if csw else "")
+    ((8, 8, 8, 16), 0.3, 0, 0.0, 1e-4),
+    ((8, 8, 8, 16), 0.6, 0, 0.0, 1e-4),
+    ((16, 16, 16, 32), 0.5, 0, 0.0, 1e-3),
+    ((16, 16, 16, 32), 0.5, 0, 1.91, 1e-3),
+    ((16, 16, 16, 32), 0.3, 0, 0.0, 1e-4),
+    ((16, 16, 16, 32), 0.6, 0, 0.0, 1e-4),
+    ((24, 24, 24, 48), 0.5, 0, 0.0, 5e-4),
+    ((32, 32, 32, 64), 0.6, 0, 0.0, 1e-4),
+    ((24, 24, 24, 48), 0.3, 0, 0.0, 1e-4),
+    ((24, 24, 24, 48), 0.6, 0, 0.0, 1e-4),
+]
+M, K = 60, 20
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default=None)
+    ap.add_argument("--max-matvecs", type=int, default=8000)
     args = ap.parse_args()
     data = {}
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    for dims, eps, seed, m, csw in [f + (0.0,) for f in FIELDS] + CLOVER_FIELDS:
-        k = key(dims, eps, seed, csw)
+    for dims, eps, seed, csw, tol in FIELDS:
+        k = fg.edge_key(dims, eps, seed, csw)
         if args.only and args.only != k:
             continue
-        if k in data and data[k].get("arnoldi_steps") == m:
+        old = data.get(k, {})
+        if old.get("method") == "krylov_schur" and old.get("tol") == tol and old.get("converged"):
             continue
         t0 = time.time()
         U = fg.gauge_field(dims, eps, seed)
         A = oracle.clover(U, dims, csw) if csw else None
-        if m > 0:
-            _, theta, bound, secs = oracle.tune_m0_arnoldi(U, dims, 0.0, m=m, clov=A)
-            how = {"arnoldi_steps": m}
-        else:
-            _, theta, bound, mv, secs = oracle.tune_m0_schur(U, dims, 0.0, m=60, k=20, tol=2e-3, clov=A)
-            how = {"arnoldi_steps": 0, "krylov_schur": {"m": 60, "k": 20, "tol": 2e-3, "matvecs": mv}}
-        if csw:
-            how["csw"] = csw
-        data[k] = {"dims": list(dims), "eps": eps, "seed": seed, **how,
-                   "edge_re": float(theta.real), "edge_im": float(theta.imag), "ritz_residual_bound": float(bound),
+
+        def log(restart, mv, theta, res):
+            print(f"{k} restart {restart} matvecs {mv} theta {theta.real:.9f}{theta.imag:+.6f}i residual {res:.3e} "
+                  f"{time.time() - t0:.0f}s", flush=True)
+
+        max_restarts = max(1, (args.max_matvecs - M) // (M - K) + 1)
+        _, theta, res, mv, secs = oracle.tune_m0_schur(U, dims, 0.0, m=M, k=K, tol=tol, clov=A,
+                                                       max_restarts=max_restarts, log=log)
+        data[k] = {"dims": list(dims), "eps": eps, "seed": seed, "method": "krylov_schur", "m": M, "k": K,
+                   "tol": tol, "matvecs": mv, "converged": bool(res < tol),
+                   "edge_re": float(theta.real), "edge_im": float(theta.imag), "ritz_residual": float(res),
                    "seconds": round(time.time() - t0, 1)}
+        if csw:
+            data[k]["csw"] = csw
         print(k, data[k], flush=True)
         with open(OUT + ".tmp", "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
         os.replace(OUT + ".tmp", OUT)
-        del U
+        del U, A
 
 
 if __name__ == "__main__":

@@ -183,20 +183,21 @@ int dw_create(const dw_lattice* L, void* cuda_stream, dw_ctx** out) {
     g.V = 1;
     g.B = 1;
     g.ndom = 1;
+    long long V = 0;
+    if (!lattice_volume(L->dims, kMaxSites, &V))
+        return fail(DW_EINVAL, "lattice extents must be >= 2 with at most 2^31/24 sites in all");
     for (int j = 0; j < 4; ++j) {
         const int d = L->dims[j], b = L->block[j];
-        if (d < 2) return fail(DW_EINVAL, "lattice extent must be >= 2");
         if (b < 1 || d % b != 0) return fail(DW_EINVAL, "block must divide the lattice extent");
         if ((d / b) % 2 != 0) return fail(DW_EINVAL, "domain count per direction must be even (red-black)");
         g.d[j] = d;
         g.b[j] = b;
         g.nb[j] = d / b;
-        g.V *= d;
         g.B *= b;
         g.ndom *= d / b;
     }
+    g.V = V;
     if (g.B > 1024) return fail(DW_EINVAL, "domain volume must be <= 1024 sites");
-    if (g.V > (1LL << 31) / 24) return fail(DW_EINVAL, "lattice too large");
     dw_ctx* c = new (std::nothrow) dw_ctx();
     if (!c) return fail(DW_ENOMEM, "host allocation failed");
     c->g = g;

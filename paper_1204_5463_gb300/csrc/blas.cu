@@ -11,6 +11,7 @@
 //         would otherwise cap these HBM-bound sweeps far below bandwidth.
 // Reductions are deterministic: every CTA writes its partial sums (FP64) to a
 // fixed slot and one CTA per right-hand side adds the slots in order.
+#include <atomic>
 #include <mutex>
 #include <set>
 
@@ -709,11 +710,17 @@ int launch_multidot(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, i
     // wave would run alone after it); at most nblk slots
     if (nv_active < 1 || nv_active > nvmax) nv_active = nvmax;
     const int ngroups = (nv_active + kDotG - 1) / kDotG;  // groups past every rhs's nv would only read w
-    static int sms[64] = {0};
+    // SM count per device, cached; the serving workers call this concurrently,
+    // so the cache entries are atomics (every writer stores the same value)
+    static std::atomic<int> sms[64];
     int dev0 = 0;
     DW_CUDA_TRY(cudaGetDevice(&dev0));
-    if (dev0 < 64 && sms[dev0] == 0) DW_CUDA_TRY(cudaDeviceGetAttribute(&sms[dev0], cudaDevAttrMultiProcessorCount, dev0));
-    const long long slots = 2LL * ((dev0 < 64 && sms[dev0] > 0) ? sms[dev0] : 152);
+    int nsm = (dev0 < 64) ? sms[dev0].load(std::memory_order_relaxed) : 0;
+    if (nsm == 0) {
+        DW_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev0));
+        if (dev0 < 64) sms[dev0].store(nsm, std::memory_order_relaxed);
+    }
+    const long long slots = 2LL * (nsm > 0 ? nsm : 152);
     long long nb = slots / ngroups;
     if (nb > nblk) nb = nblk;
     if (nb > (n + kT - 1) / kT) nb = (n + kT - 1) / kT;

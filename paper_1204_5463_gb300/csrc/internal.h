@@ -26,6 +26,24 @@ int fail(int code, const std::string& msg);
             return ::dwk::fail(DW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));   \
     } while (0)
 
+// Largest lattice a context accepts: spinor element indices (24 reals per
+// site) stay below 2^31, so device code may use 32-bit site arithmetic.
+constexpr long long kMaxSites = (1LL << 31) / 24;
+
+// V = d1 d2 d3 d4 for caller-supplied extents, checked as it is formed: every
+// extent >= 2 and the running product <= max_sites (so the product can neither
+// overflow nor wrap to a small value). Returns false with *V untouched otherwise.
+inline bool lattice_volume(const int* dims, long long max_sites, long long* V) {
+    long long v = 1;
+    for (int j = 0; j < 4; ++j) {
+        if (dims[j] < 2 || dims[j] > max_sites) return false;
+        v *= dims[j];
+        if (v > max_sites) return false;
+    }
+    *V = v;
+    return true;
+}
+
 // Every kernel launch of the library is followed by DW_LAUNCH_CHECK(): it
 // counts the launch (dw_kernel_launches()) and turns a launch error into DW_ECUDA.
 void count_launch();

@@ -50,14 +50,15 @@ extern "C" int dw_apply_f32_noalloc(const int* dims, double m0, const double* U,
     g.V = 1;
     g.B = 1;
     g.ndom = 1;
+    // the size check runs on the partial products, so huge extents cannot
+    // overflow or wrap to a volume that seems to fit the scratch
+    if (!lattice_volume(dims, kNoAllocMaxSites, &g.V))
+        return fail(DW_EINVAL,
+                    "dw_apply_f32_noalloc needs extents >= 2 and at most 4096 sites (scratch is a fixed device array)");
     for (int j = 0; j < 4; ++j) {
-        if (dims[j] < 2) return fail(DW_EINVAL, "lattice extent must be >= 2");
         g.d[j] = g.b[j] = dims[j];
         g.nb[j] = 1;
-        g.V *= dims[j];
     }
-    if (g.V > kNoAllocMaxSites)
-        return fail(DW_EINVAL, "dw_apply_f32_noalloc handles at most 4096 sites (scratch is a fixed device array)");
     char* base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;

@@ -65,9 +65,13 @@ struct dw_server {
 
 namespace {
 
+// SIZE_MAX for a lattice no context accepts (extents < 2 or too many sites),
+// so that such a request exceeds every budget.
 size_t request_bytes(const dw_request* q) {
-    long long V = 1;
-    for (int j = 0; j < 4; ++j) V *= q->lattice.dims[j];
+    long long V = 0;
+    if (!dwk::lattice_volume(q->lattice.dims, dwk::kMaxSites, &V)) return SIZE_MAX;
+    for (int j = 0; j < 4; ++j)
+        if (q->lattice.block[j] < 1 || q->lattice.dims[j] % q->lattice.block[j] != 0) return SIZE_MAX;
     const dw_solver_params& P = q->params;
     const int sp = (int)P.sap_prec;
     const bool half = (sp == dwk::P16 || sp == dwk::PB16);
@@ -250,7 +254,10 @@ int dw_server_submit(dw_server* s, const dw_request* r, uint64_t* id) {
     const dw_solver_params& P = r->params;
     if (P.nrhs < 1 || P.nrhs > DW_MAX_RHS || P.m < 1 || P.m > 63 || P.k < 0 || P.k >= P.m || P.k > 16)
         return fail(DW_EINVAL, "bad solver parameters");
+    long long V = 0;
+    if (!lattice_volume(r->lattice.dims, kMaxSites, &V)) return fail(DW_EINVAL, "bad lattice extents");
     const size_t bytes = request_bytes(r);
+    if (bytes == SIZE_MAX) return fail(DW_EINVAL, "bad lattice or domain block");
     if (bytes > s->budget) return fail(DW_ENOMEM, "request larger than the whole memory budget");
     std::lock_guard<std::mutex> lock(s->mu);
     const uint64_t k = s->next_id++;

@@ -72,6 +72,8 @@ extern "C" int dw_autotune_block(const dw_lattice* L, const double* U, const dou
                                  void* cuda_stream, int* best_block, dw_tune_entry* results, int max_results,
                                  int* n_results) {
     if (!L || !U || !b || !P || !best_block) return fail(DW_EINVAL, "null argument");
+    long long V = 0;
+    if (!lattice_volume(L->dims, kMaxSites, &V)) return fail(DW_EINVAL, "bad lattice extents");
     const Key key = make_key(L, P);
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -84,8 +86,6 @@ extern "C" int dw_autotune_block(const dw_lattice* L, const double* U, const dou
     }
     const auto cands = candidates(L->dims, (int)P->sap_prec);
     if (cands.empty()) return fail(DW_EINVAL, "no admissible domain block for this lattice");
-    long long V = 1;
-    for (int j = 0; j < 4; ++j) V *= L->dims[j];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     DevBuf x;
     x.st = st;

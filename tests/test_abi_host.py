@@ -55,6 +55,22 @@ def test_error_reporting_without_gpu_work(dw):
         dw.dw_create((4, 4, 4, 4), (4, 4, 4, 4), 0.0)  # one domain per direction: no red-black
 
 
+# extents whose product overflows 64 bits or wraps to a small value
+WRAPPING_DIMS = [(1 << 16, 1 << 16, 1 << 16, 1 << 16), (2, 1 << 30, 1 << 30, 1 << 30), (2, 2, 2, -2),
+                 ((1 << 31) - 1, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("dims", WRAPPING_DIMS)
+def test_huge_or_wrapping_extents_are_rejected_before_any_gpu_work(dw, dims):
+    with pytest.raises(dw.DwError) as e:
+        dw.dw_create(dims, (2, 2, 2, 2), 0.0)
+    assert e.value.code == dw.DW_EINVAL
+    with pytest.raises(dw.DwError) as e:
+        dw.dw_apply_f32_noalloc(dims, 0.0, 16, 16, 16)  # never dereferenced: rejected first
+    assert e.value.code == dw.DW_EINVAL
+    assert "4096" in dw.dw_last_error()
+
+
 def _crand(rng, *shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 

@@ -1,12 +1,15 @@
 """The allocation-free operator entry point, for callers that cannot call
-cudaMalloc: its FP32 result must match dw_apply's FP32 result on the same
-inputs, on consecutive calls that reuse its fixed device scratch array.
+cudaMalloc (code inside a pre-reserved memory pool, allocators that forbid
+device allocation): on consecutive calls that reuse its fixed device scratch
+array, its FP32 result must match dw_apply's FP32 result and the FP64 oracle's
+D, and a call after the first must leave the device's free memory unchanged.
 (Collected last on purpose: it shares one device array across calls.)"""
 
 import numpy as np
 import pytest
 
 import fieldgen as fg
+import oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -22,7 +25,7 @@ def _host(t, shape):
     return t.cpu().numpy().view(np.complex128).reshape(shape)
 
 
-def test_noalloc_matches_dw_apply_on_two_calls():
+def test_noalloc_matches_dw_apply_and_oracle_on_two_calls():
     import paper_1204_5463_gb300 as dw
 
     dims = (4, 4, 6, 8)  # 768 sites: several thread blocks and a ragged tail
@@ -42,8 +45,31 @@ def test_noalloc_matches_dw_apply_on_two_calls():
             dw.dw_apply_f32_noalloc(dims, m0, Ud, pin, got, stream)
             a, b = _host(got, psi.shape), _host(ref, psi.shape)
             assert np.abs(a - b).max() <= TOL_F32 * np.abs(b).max()
+            exact = oracle.dw(U, psi, dims, m0)
+            assert np.abs(a - exact).max() <= TOL_F32 * np.abs(exact).max()
     finally:
         dw.dw_destroy(ctx)
+
+
+def test_noalloc_call_leaves_free_device_memory_unchanged():
+    import paper_1204_5463_gb300 as dw
+
+    dims = (4, 4, 4, 8)
+    m0 = 0.1
+    U = fg.gauge_field(dims, 0.4, seed=5)
+    psi = fg.gaussian_source(dims, 6)
+    Ud, pin = _dev(U), _dev(psi)
+    out = torch.empty_like(pin)
+    stream = torch.cuda.current_stream().cuda_stream
+    dw.dw_apply_f32_noalloc(dims, m0, Ud, pin, out, stream)  # set-up call on this device
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        dw.dw_apply_f32_noalloc(dims, m0, Ud, pin, out, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    exact = oracle.dw(U, psi, dims, m0)
+    assert np.abs(_host(out, psi.shape) - exact).max() <= TOL_F32 * np.abs(exact).max()
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
