@@ -3,16 +3,27 @@
 
 One step = one complete solve (every stage of the path: SAP sweeps, the
 Arnoldi product, Gram-Schmidt, Givens/least squares, deflated restarts and
-the explicit FP64 residual) of the 16^3 x 32 Wilson workload: links
-U = exp(i eps H) with eps = 0.5, bare mass tuned so the smallest |eigenvalue|
-of D is about 1e-2, 4^4 domains, SAP 5 cycles x 4 MR steps, FGMRES-DR m = 30
+the explicit residual) of the 16^3 x 32 Wilson workload: links
+U = exp(i eps H) with eps = 0.5, bare mass putting the leftmost eigenvalue of
+D at real part 1e-2, 4^4 domains, SAP 5 cycles x 4 MR steps, FGMRES-DR m = 30
 k = 10, tol 1e-10, one Gaussian right-hand side. Inputs are resident in HBM
 when the timed region starts (the Krylov working set, > 1 GB, exceeds L2).
+
+The same JSON line carries the other workloads as legs: 12 right-hand sides
+with FP16 SAP on the same lattice (the mixed-precision batched solver against
+the plain one), the single-precision Arnoldi basis, FP64 outer vectors, the
+clover operator, the stencil alone (GB/s against the measured HBM peak), the
+SAP sweep's ALU roofline on three lattices, SAP as a stand-alone solver around
+the spectral edge, the batched 24^3 x 48 point-source solve on the autotuned
+block, the ill-conditioned 32^3 x 64 solve (FP16/BF16 SAP, FGMRES-DR(40,16)
+against FGMRES(40)), the served Poisson stream (p50/p99 latency), the
+conditioning of every workload, and the oracle's time for one complete solve
+(cpu_baseline).
 
 Prints one JSON line (rank 0). Under torchrun every rank solves its own
 right-hand side (replicas; no data-path collective) and the timing is the
 maximum over ranks. ``--impl reference`` times the FP64 CPU oracle on this
-host's cores instead, on a bounded sample of the same solve.
+host's cores instead, in pieces of real solves of the same workload.
 """
 
 from __future__ import annotations
@@ -215,15 +226,41 @@ def oracle_kernels(cfg, U, b):
     return {"dw_GB/s": 960.0 * V / t_dw / 1e9, "dw_s": t_dw, "sap_application_s": t_sap}
 
 
-def oracle_sample(cfg, U, b, n_iter):
-    """Seconds per Arnoldi step of the oracle on this workload (bounded sample)."""
+def oracle_solve_chunks(cfg, U, b):
+    """A generator over a complete FP64 oracle solve of this workload
+    (Algorithm 4 with the refinement of Sec. 5.7), one Arnoldi step per item."""
     import oracle
 
+    A, M = oracle.lattice_operators(U, cfg["dims"], cfg["block"], cfg["m0"], cfg["sap_cycles"], cfg["mr_steps"])
+    return oracle.fgmresdr_steps(A, M, b.reshape(-1), cfg["m"], cfg["k"], cfg["tol"])
+
+
+def oracle_full_solve(cfg, U, b):
+    """Seconds and Arnoldi steps of one complete oracle solve of this workload."""
     t0 = time.perf_counter()
-    res = oracle.solve(U, b, cfg["dims"], cfg["block"], cfg["m0"], cfg["sap_cycles"], cfg["mr_steps"], cfg["m"],
-                       cfg["k"], cfg["tol"], max_iterations=n_iter)
-    dt = time.perf_counter() - t0
-    return dt / max(1, res.iterations), res.iterations
+    it = oracle_solve_chunks(cfg, U, b)
+    steps = 0
+    for _ in it:
+        steps += 1
+    return time.perf_counter() - t0, steps
+
+
+def conditioning():
+    """min |eigenvalue| of each workload's D at its bare mass (harmonic Ritz
+    values of the oracle's D, stored with the spectral edges)."""
+    import fieldgen as fg
+
+    out = {}
+    edges = fg.spectral_edges()
+    for name, c in fg.lattice_configs().items():
+        e = edges.get(fg.edge_key(c["dims"], c["eps"], c["seed"], c.get("csw", 0.0)))
+        if not e or c.get("target_min_abs_eig") is None:
+            continue
+        ok = e.get("delta_ref") == c["target_min_abs_eig"]
+        out[name] = {"delta": c["target_min_abs_eig"], "m0": c["m0"],
+                     "min_abs_eig": e.get("min_abs_eig_at_m0_ref") if ok else None,
+                     "method": e.get("method"), "converged": e.get("converged")}
+    return out
 
 
 def max_over_ranks(values, dist=None, device="cuda"):
@@ -252,6 +289,14 @@ def cores():
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle as it stands, on this host's
+    cores, timed in pieces of real solves of the benchmark workload. Each step
+    advances a running oracle solve by a fixed number of Arnoldi steps (with
+    the cycle ends, deflated restarts and explicit residuals that fall in it);
+    a solve that finishes is followed by a new one. solves/s = Arnoldi steps
+    done / steps of a complete oracle solve / seconds; the step count of a
+    complete solve is the one the timed region finished, else the stored
+    count of the same solve (tests/golden)."""
     if rank != 0:
         return 0
     import fieldgen as fg
@@ -259,57 +304,94 @@ def run_reference(args, rank, world):
     cfg = workload()
     U = fg.gauge_field(cfg["dims"], cfg["eps"], cfg["seed"])
     b = fg.gaussian_source(cfg["dims"], 1)
-    iters_per_solve = args.ref_iterations
+    stored = stored_oracle_steps()
+    n_est = stored or 80
+    chunk = args.ref_chunk or max(1, -(-n_est // max(1, args.steps)))  # the K steps cover about one solve
+    warm = oracle_solve_chunks(cfg, U, b)
     for _ in range(args.warmup):
-        oracle_sample(cfg, U, b, 1)
-    total = 0.0
-    per = []
+        next(warm, None)
+    del warm
+    solve = oracle_solve_chunks(cfg, U, b)
+    done_steps, finished, per = 0, [], []
+    cur = 0
     for _ in range(args.steps):
-        t_it, _ = oracle_sample(cfg, U, b, 2)
-        per.append(t_it * iters_per_solve)
-        total += t_it * iters_per_solve
-    value = args.steps / total
+        t0 = time.perf_counter()
+        for _ in range(chunk):
+            if next(solve, None) is None:
+                finished.append(cur)
+                cur = 0
+                solve = oracle_solve_chunks(cfg, U, b)
+                if next(solve, None) is None:
+                    break
+            cur += 1
+            done_steps += 1
+        per.append(time.perf_counter() - t0)
+    total = sum(per)
+    steps_per_solve = finished[0] if finished else n_est
+    value = done_steps / steps_per_solve / total
+    sample = (f"{args.steps} pieces of {chunk} Arnoldi steps of a running FP64 oracle solve "
+              f"({done_steps} steps, {len(finished)} solve(s) finished; {steps_per_solve} steps per solve, "
+              + ("measured" if finished else "stored") + ")")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": cfg["dims"], "block": cfg["block"], "m0": cfg["m0"],
                    "m": cfg["m"], "k": cfg["k"], "sap": [cfg["sap_cycles"], cfg["mr_steps"]], "tol": cfg["tol"]},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores(), "kind": "oracle",
-                         "sample": f"2 Arnoldi steps of the FP64 oracle per step, extrapolated to "
-                                   f"{iters_per_solve} steps per solve (the GPU solve's count)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args, rank, world):
+def stored_oracle_steps():
+    """Arnoldi steps of the oracle's complete solve of the benchmark workload,
+    as stored by tests/golden/make_golden.py (None when not stored for the
+    current bare mass)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", WORKLOAD + "_oracle.json")) as f:
+            g = json.load(f)
+    except Exception:
+        return None
+    if abs(g["config"]["m0"] - workload()["m0"]) > 1e-12:
+        return None
+    return int(g["iterations"])
+
+
+def _dev(a):
+    import numpy as np
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).reshape(-1).copy()).cuda()
+
+
+def serving_leg(args, rank):
     """Continuous-batching serving of a Poisson stream of mixed solves.
 
     Requests: volumes uniform in {8^3x16, 16^3x32, 24^3x48}, eps in {0.3, 0.6},
     bare mass with the left spectral edge at delta ~ log-uniform[1e-3, 1e-2],
     1-12 Gaussian right-hand sides, tol 1e-10, FP16 SAP storage; arrivals
-    Poisson at --rate req/s (seeded); server budget 150 GB of device memory.
+    Poisson at --rate req/s (seeded) over a fixed window of --window seconds;
+    server budget 150 GB of device memory; latency = submit to done, drain
+    included.
     """
     import threading
 
     import numpy as np
-    import torch
 
     import fieldgen as fg
     import paper_1204_5463_gb300 as dw
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rng = np.random.default_rng(1234 + rank)
     vols = [(8, 8, 8, 16), (16, 16, 16, 32), (24, 24, 24, 48)]
     epss = [0.3, 0.6]
     fields = {(d, e): fg.gauge_field(d, e, seed=0) for d in vols for e in epss}
     edges = fg.spectral_edges()
     reqs = []
-    t = 0.0
-    for i in range(args.requests):
-        t += rng.exponential(1.0 / args.rate)
+    t = rng.exponential(1.0 / args.rate)
+    i = 0
+    while t < args.window:
         d = vols[rng.integers(len(vols))]
         e = epss[rng.integers(len(epss))]
         delta = float(np.exp(rng.uniform(np.log(1e-3), np.log(1e-2))))
@@ -317,6 +399,8 @@ def run_serving(args, rank, world):
         nrhs = int(rng.integers(1, 13))
         b = np.ascontiguousarray(fg.gaussian_source(d, 5000 + i, nrhs=nrhs))
         reqs.append(dict(t=t, dims=d, eps=e, m0=m0, delta=delta, nrhs=nrhs, b=b, x=np.zeros_like(b)))
+        t += rng.exponential(1.0 / args.rate)
+        i += 1
     srv = dw.dw_server_create(int(150e9), args.slots)  # 150 GB budget
     keep = []
     ids = [None] * len(reqs)
@@ -346,117 +430,186 @@ def run_serving(args, rank, world):
     wall = time.perf_counter() - t_start
     info = dw.dw_server_info(srv)
     dw.dw_server_destroy(srv)
-    line = {
+    return {
         "metric": "served SAP-FGMRES-DR solves/s (continuous batching, HBM budget 150 GB)",
-        "value": solved / wall, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-        "requests": len(reqs), "requests_ok": ok, "rhs_solved": solved,
-        "offered_req_per_s": args.rate, "achieved_req_per_s": len(reqs) / wall, "wall_s": wall,
+        "value": solved / wall, "unit": "solves/s", "requests": len(reqs), "requests_ok": ok,
+        "rhs_solved": solved, "arrival_window_s": args.window, "offered_req_per_s": args.rate,
+        "achieved_req_per_s": len(reqs) / wall, "wall_s": wall,
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(max(lat))},
-        "peak_hbm_gb": info["peak_bytes"] / 1e9, "slots": args.slots,
+        "peak_hbm_gb": info["peak_bytes"] / 1e9, "slots": args.slots, "peak_running": info["peak_running"],
         "dtype": "f16 SAP, f32 D z, " + ("FP32 Arnoldi basis with double-float residual" if args.serving_outer == "f32"
                                          else "double-float Arnoldi basis and residual"),
-        "data": "synthetic",
         "config": {"workload": "serving: volumes {8^3x16,16^3x32,24^3x48}, eps {0.3,0.6}, "
-                               "min|lambda| log-uniform [1e-3,1e-2], 1-12 rhs, tol 1e-10, m 30, k 10, SAP 5x4"},
+                               "leftmost eigenvalue at delta log-uniform [1e-3,1e-2], 1-12 rhs, tol 1e-10, m 30, "
+                               "k 10, SAP 5x4"},
+        "note": "the offered rate exceeds the service rate, so latency grows with the queue over the window",
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_workload(args, rank, world):
-    """The batched (24^3x48, 12 point sources) and mixed-precision (32^3x64,
-    FP16/BF16 SAP, FGMRES-DR(40,16) vs restarted FGMRES(40)) workloads."""
-    import numpy as np
+def _profiled_sap(dw, torch, ctx, bd, ncyc, nmr, prec, nrhs, V, block):
+    """Average SAP sweep of one preconditioner application (per-kernel events)."""
+    zd = torch.empty_like(bd)
+    dw.sap_precondition(ctx, bd, zd, ncyc, nmr, prec, nrhs)
+    dw.dw_profile(ctx, True)
+    dw.dw_profile_read(ctx, reset=True)
+    for _ in range(3):
+        dw.sap_precondition(ctx, bd, zd, ncyc, nmr, prec, nrhs)
+    torch.cuda.synchronize()
+    d = dw.dw_profile_read(ctx, reset=True)["sap_sweep"]
+    dw.dw_profile(ctx, False)
+    avg_s = d["total_ms"] / d["launches"] / 1e3
+    flops = nrhs * (V / 2) * sap_flops_per_site(block, nmr)
+    tf = flops / avg_s / 1e12
+    return {"nrhs": nrhs, "avg_us": avg_s * 1e6, "us_per_rhs": avg_s * 1e6 / nrhs, "achieved_tflops": tf,
+            "frac": tf / FP32_PEAK_TFLOPS, "launches": d["launches"]}
+
+
+def _solve_on(dw, torch, dims, block, m0, Ud, b, **kw):
+    ctx = dw.dw_create(dims, block, m0, torch.cuda.current_stream().cuda_stream)
+    try:
+        dw.dw_set_gauge(ctx, Ud, True)
+        P = dw.dw_default_params(**kw)
+        bd = _dev(b)
+        xd = torch.zeros_like(bd)
+        dw.fgmresdr_solve(ctx, bd, xd, P, allow_notconv=True)  # warm-up: workspace and link copies
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = dw.fgmresdr_solve(ctx, bd, xd, P, allow_notconv=True)
+        torch.cuda.synchronize()
+        return S, time.perf_counter() - t0
+    finally:
+        dw.dw_destroy(ctx)
+
+
+def mixed_leg(args):
+    """The ill-conditioned 32^3 x 64 workload (leftmost eigenvalue of D at
+    1e-3): FP16 and BF16 SAP storage, FGMRES-DR(40, 16) against restarted
+    FGMRES(40) (capped at --k0-cycles cycles); and the FP32 SAP sweep alone on
+    this lattice (its ALU roofline at 4096 domains per colour)."""
     import torch
 
     import fieldgen as fg
     import paper_1204_5463_gb300 as dw
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cfg = dict(fg.lattice_configs()[WORKLOAD if args.workload == "sap_standalone" else args.workload])
+    cfg = dict(fg.lattice_configs()["mixed_32x32x32x64"])
     dims = cfg["dims"]
-    stream = torch.cuda.current_stream()
-
-    def dev(a):
-        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).reshape(-1).copy()).cuda()
-
     U = fg.gauge_field(dims, cfg["eps"], cfg["seed"])
-    Ud = dev(U)
-    out = {"workload": args.workload, "lattice": list(dims), "m0": cfg["m0"], "eps": cfg["eps"],
-           "target_min_abs_eig": cfg["target_min_abs_eig"], "runs": []}
+    Ud = _dev(U)
+    del U
+    b = fg.gaussian_source(dims, 1)
+    edges = fg.spectral_edges().get(fg.edge_key(dims, cfg["eps"], cfg["seed"]), {})
+    out = {"lattice": list(dims), "m0": cfg["m0"], "eps": cfg["eps"], "delta": cfg["target_min_abs_eig"],
+           "min_abs_eig": edges.get("min_abs_eig_at_m0_ref"), "runs": []}
+    for prec, pname in ((dw.DW_F16, "f16"), (dw.DW_BF16, "bf16")):
+        for k, cyc in ((cfg["k"], 400), (0, args.k0_cycles)):
+            S, dt = _solve_on(dw, torch, dims, cfg["block"], cfg["m0"], Ud, b, m=cfg["m"], k=k, tol=cfg["tol"],
+                              sap_cycles=cfg["sap_cycles"], mr_steps=cfg["mr_steps"], sap_prec=prec,
+                              matvec_prec=dw.DW_F32, max_cycles=cyc)
+            out["runs"].append({"sap_prec": pname, "m": cfg["m"], "k": k, "seconds": dt,
+                                "converged": S.converged, "iterations": S.iterations, "cycles": S.cycles,
+                                "clean_restarts": S.clean_restarts, "true_rel_res": S.true_rel_res[0]})
+    ctx = dw.dw_create(dims, cfg["block"], cfg["m0"], torch.cuda.current_stream().cuda_stream)
+    dw.dw_set_gauge(ctx, Ud, True)
+    out["sap_sweep_f32"] = _profiled_sap(dw, torch, ctx, _dev(b), cfg["sap_cycles"], cfg["mr_steps"], dw.DW_F32, 1,
+                                         fg.volume(dims), cfg["block"])
+    dw.dw_destroy(ctx)
+    return out
 
-    def solve(block, b, nrhs, **kw):
-        ctx = dw.dw_create(dims, block, cfg["m0"], stream.cuda_stream)
+
+def batched_leg(args):
+    """The batched 24^3 x 48 workload: the 12 spin-colour point sources in one
+    solve (FP16 SAP storage), on the domain block the autotuner picks by time
+    to solution; and the FP32 SAP sweep alone on this lattice."""
+    import torch
+
+    import fieldgen as fg
+    import paper_1204_5463_gb300 as dw
+
+    cfg = dict(fg.lattice_configs()["batched_24x24x24x48"])
+    dims = cfg["dims"]
+    U = fg.gauge_field(dims, cfg["eps"], cfg["seed"])
+    Ud = _dev(U)
+    del U
+    b = fg.point_sources(dims)
+    out = {"lattice": list(dims), "m0": cfg["m0"], "eps": cfg["eps"], "delta": cfg["target_min_abs_eig"]}
+    blk = tuple(cfg["block"])
+    if not args.no_tune:
+        bt, table = dw.dw_autotune_block(dims, cfg["m0"], Ud, _dev(b[:2]),
+                                         dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=1e-6, sap_cycles=5,
+                                                              mr_steps=4, nrhs=2, sap_prec=dw.DW_F16))
+        out["autotune"] = {"best": bt, "candidates": [
+            {"block": t[0], "seconds": t[1], "iterations": t[2], "status": t[3]} for t in table]}
+        blk = bt
+    S, dt = _solve_on(dw, torch, dims, blk, cfg["m0"], Ud, b, m=cfg["m"], k=cfg["k"], tol=cfg["tol"],
+                      sap_cycles=cfg["sap_cycles"], mr_steps=cfg["mr_steps"], sap_prec=dw.DW_F16,
+                      matvec_prec=dw.DW_F32, nrhs=12)
+    out.update({"block": list(blk), "nrhs": 12, "sap_prec": "f16", "seconds": dt, "value": S.converged / dt,
+                "unit": "solves/s", "converged": S.converged, "iterations_max": S.iterations, "cycles": S.cycles,
+                "true_rel_res_max": max(S.true_rel_res[i] for i in range(12))})
+    ctx = dw.dw_create(dims, cfg["block"], cfg["m0"], torch.cuda.current_stream().cuda_stream)
+    dw.dw_set_gauge(ctx, Ud, True)
+    out["sap_sweep_f32"] = _profiled_sap(dw, torch, ctx, _dev(fg.gaussian_source(dims, 1)), cfg["sap_cycles"],
+                                         cfg["mr_steps"], dw.DW_F32, 1, fg.volume(dims), cfg["block"])
+    dw.dw_destroy(ctx)
+    return out
+
+
+def sap_standalone_leg(args, cfg, Ud):
+    """SAP as a stand-alone solver (Sec. 3; the analogue of Fig. 5): the
+    relative residual after s cycles from x = 0 on the benchmark lattice, for
+    bare masses around the spectral edge of D (delta = leftmost real part of
+    spec D_m0)."""
+    import torch
+
+    import fieldgen as fg
+    import paper_1204_5463_gb300 as dw
+
+    dims = cfg["dims"]
+    edge = fg.spectral_edges()[fg.edge_key(dims, cfg["eps"], cfg["seed"])]["edge_re"]
+    bd = _dev(fg.gaussian_source(dims, 1))
+    zd = torch.empty_like(bd)
+    rd = torch.empty_like(bd)
+    out = {"lattice": list(dims), "sap_cycles_max": args.sap_cycles_max, "mr_steps": cfg["mr_steps"], "runs": []}
+    for delta in (0.3, 0.1, 0.03, 0.01, -0.01, -0.03, -0.1):
+        m0 = delta - edge
+        ctx = dw.dw_create(dims, cfg["block"], m0, torch.cuda.current_stream().cuda_stream)
         try:
             dw.dw_set_gauge(ctx, Ud, True)
-            opts = dict(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
-                        mr_steps=cfg["mr_steps"], nrhs=nrhs)
-            opts.update(kw)
-            P = dw.dw_default_params(**opts)
-            bd = dev(b)
-            xd = torch.zeros_like(bd)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            S = dw.fgmresdr_solve(ctx, bd, xd, P, allow_notconv=True)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            return S, dt
+            hist = []
+            for s_ in range(1, args.sap_cycles_max + 1):
+                dw.sap_precondition(ctx, bd, zd, s_, cfg["mr_steps"], dw.DW_F32, 1)
+                dw.dw_apply(ctx, zd, rd, dw.DW_F64, 1)
+                hist.append(float(torch.linalg.vector_norm(bd - rd) / torch.linalg.vector_norm(bd)))
         finally:
             dw.dw_destroy(ctx)
+        best = min(range(len(hist)), key=lambda i: hist[i])
+        out["runs"].append({"delta": delta, "m0": m0, "kappa": 1.0 / (2.0 * (4.0 + m0)),
+                            "rel_res_by_cycle": [round(h, 9) for h in hist], "min_at_cycle": best + 1,
+                            "diverges": hist[-1] > 2 * hist[best]})
+    return out
 
-    if args.workload == "sap_standalone":
-        # SAP as a stand-alone solver (the analogue of the paper's Fig. 5): the
-        # relative residual after s cycles from x = 0, for bare masses around
-        # the spectral edge of D (delta = smallest real part of spec D_m0)
-        import fieldgen as fg2
 
-        edge = fg2.spectral_edges()[fg2.edge_key(dims, cfg["eps"], cfg["seed"])]["edge_re"]
-        b = fg.gaussian_source(dims, 1)
-        bd = dev(b)
-        zd = torch.empty_like(bd)
-        rd = torch.empty_like(bd)
-        out["sap_cycles_max"] = args.sap_cycles_max
-        for delta in (0.3, 0.1, 0.03, 0.01, -0.01, -0.03):
-            m0 = delta - edge
-            ctx = dw.dw_create(dims, cfg["block"], m0, stream.cuda_stream)
-            try:
-                dw.dw_set_gauge(ctx, Ud, True)
-                hist = []
-                for s_ in range(1, args.sap_cycles_max + 1):
-                    dw.sap_precondition(ctx, bd, zd, s_, cfg["mr_steps"], dw.DW_F32, 1)
-                    dw.dw_apply(ctx, zd, rd, dw.DW_F64, 1)
-                    hist.append(float(torch.linalg.vector_norm(bd - rd) / torch.linalg.vector_norm(bd)))
-            finally:
-                dw.dw_destroy(ctx)
-            out["runs"].append({"delta": delta, "m0": m0, "kappa": 1.0 / (2.0 * (4.0 + m0)),
-                                "rel_res_by_cycle": hist})
+def run_workload(args, rank, world):
+    """One extra leg alone (--workload batched_24x24x24x48, mixed_32x32x32x64 or
+    sap_standalone, or --serving), printed as its own JSON line."""
+    import torch
+
+    import fieldgen as fg
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.serving:
+        out = serving_leg(args, rank)
+    elif args.workload == "sap_standalone":
+        cfg = workload()
+        out = sap_standalone_leg(args, cfg, _dev(fg.gauge_field(cfg["dims"], cfg["eps"], cfg["seed"])))
     elif args.workload.startswith("batched"):
-        b = fg.point_sources(dims)
-        blocks = [tuple(cfg["block"])]
-        if not args.no_tune:
-            bt, table = dw.dw_autotune_block(dims, cfg["m0"], Ud, dev(b[:2]),
-                                             dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=1e-6, sap_cycles=5,
-                                                                  mr_steps=4, nrhs=2, sap_prec=dw.DW_F16))
-            out["autotune"] = {"best": bt, "candidates": [
-                {"block": t[0], "seconds": t[1], "iterations": t[2], "status": t[3]} for t in table]}
-            if bt not in blocks:
-                blocks.append(bt)
-        for blk in blocks:
-            S, dt = solve(blk, b, 12, sap_prec=dw.DW_F16)
-            out["runs"].append({"block": list(blk), "nrhs": 12, "sap_prec": "f16", "seconds": dt,
-                                "solves_per_s": S.converged / dt, "converged": S.converged,
-                                "iterations_max": S.iterations, "cycles": S.cycles,
-                                "true_rel_res_max": max(S.true_rel_res[i] for i in range(12))})
+        out = batched_leg(args)
+    elif args.workload.startswith("mixed"):
+        out = mixed_leg(args)
     else:
-        b = fg.gaussian_source(dims, 1)
-        for prec, pname in ((dw.DW_F16, "f16"), (dw.DW_BF16, "bf16")):
-            for k, cyc in ((cfg["k"], 400), (0, args.k0_cycles)):
-                S, dt = solve(cfg["block"], b, 1, sap_prec=prec, k=k, max_cycles=cyc)
-                out["runs"].append({"sap_prec": pname, "m": cfg["m"], "k": k, "seconds": dt,
-                                    "converged": S.converged, "iterations": S.iterations, "cycles": S.cycles,
-                                    "clean_restarts": S.clean_restarts, "true_rel_res": S.true_rel_res[0]})
+        raise SystemExit(f"unknown workload {args.workload}")
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
@@ -468,16 +621,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-iterations", type=int, default=81,
-                    help="Arnoldi steps per solve used to scale the reference sample (the GPU solver's count on "
-                         "this workload)")
+    ap.add_argument("--ref-chunk", type=int, default=0,
+                    help="Arnoldi steps of the oracle per reference-arm step (0: the K steps cover one solve)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the legs of the other workloads (mixed 32^3x64, batched 24^3x48, serving, "
+                         "stand-alone SAP)")
     ap.add_argument("--sap-prec", default="f32")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-dw-bw", action="store_true", help="skip the stand-alone D_w bandwidth measurement")
     ap.add_argument("--dw-lattice", default="24x24x24x48", help="lattice of the stand-alone D_w measurement")
     ap.add_argument("--serving", action="store_true", help="run the serving measurement instead")
-    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--window", type=float, default=0.8, help="arrival window of the served Poisson stream (s)")
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serving-outer", default="df64", choices=["df64", "f32"],
@@ -505,9 +660,7 @@ def main():
             torch.cuda.set_device(local)
         # the reference arm runs the CPU oracle: gloo, no device
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
-    if args.serving:
-        return run_serving(args, rank, world)
-    if args.workload != WORKLOAD:
+    if args.serving or args.workload != WORKLOAD:
         return run_workload(args, rank, world)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)
@@ -673,6 +826,29 @@ def main():
                 "clean_restarts": S32.clean_restarts, "true_rel_res": S32.true_rel_res[0],
                 "ratio_vs_plain": sv / value}
 
+    # FP64 outer vectors (the Arnoldi basis, x, b, r and their Gram-Schmidt in
+    # native FP64) beside the double-float headline, same lattice and rhs
+    f64o = None
+    if not args.no_batched:
+        P64 = dw.dw_default_params(m=cfg["m"], k=cfg["k"], tol=cfg["tol"], sap_cycles=cfg["sap_cycles"],
+                                   mr_steps=cfg["mr_steps"], sap_prec=dw.PREC[args.sap_prec], matvec_prec=dw.DW_F32,
+                                   outer_prec=dw.DW_F64)
+        S64 = dw.fgmresdr_solve(ctx, bd, xd, P64)
+        barrier()
+        f0e, f1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0e.record(stream)
+        for _ in range(args.steps):
+            S64 = dw.fgmresdr_solve(ctx, bd, xd, P64)
+            assert S64.converged == 1 and S64.true_rel_res[0] <= cfg["tol"]
+        f1e.record(stream)
+        barrier()
+        (fms,) = max_over_ranks([f0e.elapsed_time(f1e)], dist)
+        fv = replica_throughput(args.steps, fms / 1e3, world)
+        f64o = {"value": fv, "unit": "solves/s", "outer_prec": "f64 basis, x, b, r",
+                "ms_per_step": fms / args.steps, "iterations": S64.iterations, "cycles": S64.cycles,
+                "clean_restarts": S64.clean_restarts, "true_rel_res": S64.true_rel_res[0],
+                "ratio_vs_double_float": fv / value}
+
     # the clover-improved operator (c_sw = 1.91, the paper's 16^3 x 32 value)
     # on the same links, bare mass tuned to its own spectral edge
     clov = None
@@ -722,6 +898,13 @@ def main():
     shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4) for k, v in prof.items()}
     avg_us = {k: round(1e3 * v["total_ms"] / v["launches"], 2) for k, v in prof.items() if v["launches"]}
     dwbw = None if args.no_dw_bw else dw_bandwidth(peaks, dims=tuple(int(v) for v in args.dw_lattice.split("x")))
+    sap16 = _profiled_sap(dw, torch, ctx, bd, cfg["sap_cycles"], cfg["mr_steps"], dw.DW_F32, 1, V, block)
+    extra = {}
+    if not args.no_extra:
+        extra["sap_standalone"] = sap_standalone_leg(args, cfg, Ud)
+        extra["batched_24x24x24x48"] = batched_leg(args)
+        extra["mixed_32x32x32x64"] = mixed_leg(args)
+        extra["serving"] = serving_leg(args, rank)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -746,16 +929,20 @@ def main():
         "clocks": clk,
         "mixed_batched": mb,
         "fp32_arnoldi": sp32,
+        "fp64_outer": f64o,
         "clover": clov,
         "dw_apply": dwbw,
+        "sap_sweep_by_lattice": {"16x16x16x32": sap16,
+                                 "24x24x24x48": extra.get("batched_24x24x24x48", {}).get("sap_sweep_f32"),
+                                 "32x32x32x64": extra.get("mixed_32x32x32x64", {}).get("sap_sweep_f32")},
+        "conditioning": conditioning(),
+        **extra,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        t_it, n = oracle_sample(cfg, U, b, 3)
-        per_solve = t_it * statistics.median(iters)
-        line["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores(), "kind": "oracle",
-                                "sample": f"{n} Arnoldi steps of the FP64 oracle on this workload "
-                                          f"({t_it:.2f} s/step), extrapolated to the GPU solve's "
-                                          f"{int(statistics.median(iters))} steps",
+        secs, n = oracle_full_solve(cfg, U, b)
+        line["cpu_baseline"] = {"value": 1.0 / secs, "unit": "solves/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"one complete FP64 oracle solve of this workload ({n} Arnoldi steps, "
+                                          f"{secs:.1f} s)",
                                 "kernels": oracle_kernels(cfg, U, b)}
     dw.dw_destroy(ctx)
     if rank == 0:

@@ -173,12 +173,38 @@ void dw_default_params(dw_solver_params* P);
  * G_{k+1} and v_{k+1}; a clean restart follows when
  * ||r_explicit|| / ||r_implicit|| > clean_restart_t.
  * b, x: canonical FP64 layout, nrhs fields, device pointers unless
- * P->host_buffers. Returns DW_OK when every rhs met tol, DW_ENOTCONV when a
+ * P->host_buffers. Each rhs is solved for b scaled by the power of two
+ * nearest 1/||b|| (exact; x is scaled back), so the FP32-range double-float
+ * and FP32 vectors hold any b whose norm is finite in FP64 and whose
+ * entries, relative to ||b||, stay within FP32's range.
+ * Returns DW_OK when every rhs met tol, DW_ENOTCONV when a
  * limit stopped the solve (x then holds the last iterate), or an error code
  * (DW_EINVAL, DW_ENOMEM, DW_ECUDA, DW_EBREAKDOWN, DW_ENONFINITE, and
- * DW_ETIMEOUT when a SAP sweep's bounded wait for its links gave up).
+ * DW_ETIMEOUT when a SAP sweep's bounded wait for its links gave up, and
+ * DW_ECANCELLED after dw_cancel).
  * S may be NULL. */
 int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S);
+
+/* Asks the solve running on ctx (in another thread) to stop: fgmresdr_solve
+ * checks the request before every Arnoldi step and then returns DW_ECANCELLED,
+ * with x holding the iterate of the last completed cycle and S filled as for
+ * DW_ENOTCONV. A solve clears the request when it starts, so a cancel issued
+ * while no solve runs has no effect. Safe to call from any thread. */
+int dw_cancel(dw_ctx* ctx);
+
+/* Test and diagnosis hook (not part of the paper's method): copies the bases
+ * of the last cycle of the last fgmresdr_solve on ctx for right-hand side rhs,
+ * so that the flexible Arnoldi relation A Z_m = V_{m+1} Hhat_m (Eq.
+ * "arnoldilike"; after a deflated restart its leading k columns are the
+ * rotated ones of Eq. "hatHk") and the orthonormality of V can be checked.
+ * *ncols = m', the columns of that cycle (0 if the solve stopped inside a
+ * cycle or converged before its first step). V_out: device, (m'+1) canonical
+ * FP64 fields; Z_out: device, m' fields; H_out: host, (m'+1) x m' complex,
+ * row-major, interleaved re,im, in the scaling of the solve (b scaled by the
+ * power of two nearest 1/||b||). Each output may be NULL; max_cols bounds m'
+ * (DW_EINVAL if smaller). The bases are the library's internal copies
+ * widened to FP64 (basis format outer_prec, Z in its storage format). */
+int dw_debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* dw_last_error(void);
@@ -287,6 +313,7 @@ typedef struct {
     int running, queued;
     long long completed;
     long long reused; /* requests that took over a cached context */
+    int peak_running;  /* most requests that were solving at the same time */
 } dw_server_status;
 
 typedef struct dw_server dw_server;
@@ -309,7 +336,9 @@ int dw_server_submit(dw_server* s, const dw_request* r, uint64_t* id);
 int dw_server_poll(dw_server* s, uint64_t id, int* done, int* status, dw_stats* S, double* latency_s);
 /* Blocks until the request is done or timeout_s passed (DW_ETIMEOUT). */
 int dw_server_wait(dw_server* s, uint64_t id, double timeout_s, int* status, dw_stats* S, double* latency_s);
-/* Cancels a queued request; running requests are not interrupted. */
+/* Cancels a request: a queued one is dropped at once; a running one stops
+ * before its next Arnoldi step (its status becomes DW_ECANCELLED, its x holds
+ * the iterate of its last completed cycle). DW_EINVAL if finished or unknown. */
 int dw_server_cancel(dw_server* s, uint64_t id);
 int dw_server_info(dw_server* s, dw_server_status* out);
 /* in_use_bytes includes idle cached contexts.

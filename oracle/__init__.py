@@ -296,7 +296,22 @@ class SolveResult:
 
 def fgmresdr(A, M, b, m: int, k: int, tol: float, max_cycles: int = 1000, t_clean: float = 4.0,
              x0=None, max_iterations: int | None = None, on_cycle=None) -> SolveResult:
-    """Algorithm 4 (F-GMRES-DR) with the refinement scheme of Sec. 5.7 (Algorithm 5).
+    """Algorithm 4 (F-GMRES-DR) with the refinement scheme of Sec. 5.7
+    (Algorithm 5), run to the end: see ``fgmresdr_steps`` for the readings."""
+    it = fgmresdr_steps(A, M, b, m, k, tol, max_cycles, t_clean, x0, max_iterations, on_cycle)
+    while True:
+        try:
+            next(it)
+        except StopIteration as stop:
+            return stop.value
+
+
+def fgmresdr_steps(A, M, b, m: int, k: int, tol: float, max_cycles: int = 1000, t_clean: float = 4.0,
+                   x0=None, max_iterations: int | None = None, on_cycle=None):
+    """Algorithm 4 (F-GMRES-DR) with the refinement scheme of Sec. 5.7
+    (Algorithm 5), as a generator: it yields the running SolveResult after
+    every Arnoldi step (so a caller can time a solve in pieces) and returns the
+    final SolveResult (``StopIteration.value``).
 
     Readings taken (the paper leaves these open):
 
@@ -378,6 +393,7 @@ def fgmresdr(A, M, b, m: int, k: int, tol: float, max_cycles: int = 1000, t_clea
                 V[j + 1] = w / hn
             eta, _, _, _ = np.linalg.lstsq(H[:j + 2, :j + 1], c[:j + 2], rcond=None)
             res_impl = np.linalg.norm(c[:j + 2] - H[:j + 2, :j + 1] @ eta)
+            yield res
             if breakdown or res_impl <= tol * bnorm or (
                     max_iterations is not None and res.iterations >= max_iterations):
                 mm = j + 1
@@ -515,6 +531,73 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
     if return_vector:
         return theta, bound, matvecs, V[:m].T @ y
     return theta, bound, matvecs
+
+
+def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts: int = 100, tol: float = 1e-6,
+                          nev: int = 4, seed: int = 0, log=None, return_vectors: bool = False):
+    """Eigenvalues of A nearest the origin by harmonic Ritz extraction with
+    thick restarts (the deflated restart of GMRES-DR without the linear system).
+
+    Each restart expands A V_m = V_{m+1} Hhat_m to m vectors and takes the
+    harmonic Ritz pairs of Lemma 1a: (H_m + f h_m^H) g = theta g with
+    H_m^H f = h_m, Hhat_m = [H_m; h_m^H]. The residual of a pair,
+    A u - theta u with u = V_m g, equals V_{m+1} (h_m^H g) [-f; 1], so all
+    residuals share the direction [-f; 1] and each has the norm
+    |h_m^H g| ||[-f; 1]|| / ||g||. The restart keeps the k pairs of smallest
+    |theta|: with G_{k+1} = [[G_k], [0]] | [-f; 1] orthonormalised (QR) to
+    Q_{k+1}, V_{k+1} = V_{m+1} Q_{k+1} and Hhat_k = Q_{k+1}^H Hhat_m Q_k
+    satisfy A V_k = V_{k+1} Hhat_k (Eqs. "G_kplus1", "tildeV_Vplus1",
+    "hatHk" with the eigenvector residual in place of the linear system's).
+    Stops once the nev pairs of smallest |theta| all have residual norms
+    below tol. Returns (theta[nev], residual norms[nev], matvecs), plus the
+    unit vectors u (columns of an n x nev array) with return_vectors."""
+    rng = np.random.default_rng(seed)
+    V = np.zeros((m + 1, n), dtype=np.complex128)
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    V[0] = v / np.linalg.norm(v)
+    p = 0
+    matvecs = 0
+    theta = res = None
+    for restart in range(max_restarts):
+        for j in range(p, m):
+            w = np.asarray(apply(V[j]), dtype=np.complex128)
+            matvecs += 1
+            for _pass in range(2):
+                h = (V[:j + 1] @ w.conj()).conj()
+                w = w - V[:j + 1].T @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            V[j + 1] = w / H[j + 1, j]
+        Hm = H[:m, :m]
+        hrow = H[m, :m]
+        f = np.linalg.solve(Hm.conj().T, hrow.conj())
+        lam, G = np.linalg.eig(Hm + np.outer(f, hrow))
+        order = np.argsort(np.abs(lam), kind="stable")
+        fn = np.sqrt(1.0 + np.linalg.norm(f) ** 2)
+        allres = np.abs(hrow @ G) * fn / np.linalg.norm(G, axis=0)
+        theta, res = lam[order[:nev]], allres[order[:nev]]
+        if log is not None:
+            log(restart, matvecs, theta, res)
+        if res.max() < tol or restart == max_restarts - 1:
+            if return_vectors:
+                Gs = G[:, order[:nev]]
+                U = V[:m].T @ (Gs / np.linalg.norm(Gs, axis=0))
+                return theta, res, matvecs, U
+            break
+        Gk1 = np.zeros((m + 1, k + 1), dtype=np.complex128)
+        Gk1[:m, :k] = G[:, order[:k]]
+        Gk1[:m, k] = -f
+        Gk1[m, k] = 1.0
+        Q, _ = np.linalg.qr(Gk1)
+        Hk = Q.conj().T @ H[:m + 1, :m] @ Q[:m, :k]
+        Vk1 = Q.T @ V[:m + 1]
+        V[:] = 0
+        H[:] = 0
+        V[:k + 1] = Vk1
+        H[:k + 1, :k] = Hk
+        p = k
+    return theta, res, matvecs
 
 
 def tune_m0_schur(U, dims, target: float, m: int = 60, k: int = 20, tol: float = 1e-3, seed: int = 0, clov=None,

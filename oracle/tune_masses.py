@@ -1,14 +1,26 @@
 """Writes fieldgen/spectral_edges.json: the left spectral edge of D (at m0 = 0)
-for every synthetic gauge field the workloads use, from the oracle only.
+for every synthetic gauge field the workloads use, and the eigenvalues of the
+workload's D_m0 nearest the origin, from the oracle only.
 
-The edge is the leftmost Ritz value of a thick-restarted Arnoldi process
-(Krylov-Schur, ``oracle.tune_m0_schur``) on the oracle's D, run until the
-residual norm of its Ritz pair is at most ``tol``. Since
-spec(D_m0) = spec(D_0) + m0, a workload that wants the leftmost eigenvalue of
-D at real part delta takes m0 = delta - Re(edge) (fieldgen.lattice_configs
-does this); ``tol`` is a tenth of the smallest delta the field is used with.
+spec(D_m0) = spec(D_0) + m0 exactly, so a workload that wants the leftmost
+eigenvalue of D at real part delta takes m0 = delta - edge. For each field:
 
-Usage: python -m oracle.tune_masses [--only KEY] [--max-matvecs N]
+1. start from a rough edge e0 (a stored value, else 300 products of the
+   thick-restarted Arnoldi process ``oracle.krylov_schur_edge``);
+2. compute the eigenvalues of D_{m1}, m1 = delta_ref - e0, nearest the origin
+   by harmonic Ritz extraction with thick restarts
+   (``oracle.harmonic_ritz_nearest``, Lemma 1a), until each of the nev nearest
+   has a residual ||D u - theta u|| below delta_ref / 100;
+3. edge = min Re(theta) - m1 (the leftmost of them, as an eigenvalue of D_0);
+   at the workload's m0 = delta_ref - edge its eigenvalues nearest the origin
+   are theta + (m0 - m1), so the stored min |lambda| is that of the workload's
+   operator (the verification asked for by reading R16).
+
+delta_ref is the smallest delta the field serves (1e-2 for the 16^3 x 32 bench
+and clover workloads, 5e-3 for the batched 24^3 x 48 one, 1e-3 for the mixed
+32^3 x 64 one and for the served requests).
+
+Usage: python -m oracle.tune_masses [--only KEY] [--max-restarts N]
 """
 
 from __future__ import annotations
@@ -19,6 +31,8 @@ import os
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
@@ -27,59 +41,72 @@ import oracle  # noqa: E402
 
 OUT = os.path.join(ROOT, "fieldgen", "spectral_edges.json")
 
-# (dims, eps, seed, c_sw, residual tolerance), cheapest first. The tolerance is
-# a tenth of the smallest delta the field serves: 1e-2 for the 16^3 x 32 bench
-# and clover workloads, 5e-3 for the batched 24^3 x 48 one, 1e-3 for the mixed
-# 32^3 x 64 one and for the served requests (delta in [1e-3, 1e-2]).
+# (dims, eps, seed, c_sw, delta_ref, basis m, kept k), in the order they run
 FIELDS = [
-    ((8, 8, 8, 16), 0.3, 0, 0.0, 1e-4),
-    ((8, 8, 8, 16), 0.6, 0, 0.0, 1e-4),
-    ((16, 16, 16, 32), 0.5, 0, 0.0, 1e-3),
-    ((16, 16, 16, 32), 0.5, 0, 1.91, 1e-3),
-    ((16, 16, 16, 32), 0.3, 0, 0.0, 1e-4),
-    ((16, 16, 16, 32), 0.6, 0, 0.0, 1e-4),
-    ((24, 24, 24, 48), 0.5, 0, 0.0, 5e-4),
-    ((32, 32, 32, 64), 0.6, 0, 0.0, 1e-4),
-    ((24, 24, 24, 48), 0.3, 0, 0.0, 1e-4),
-    ((24, 24, 24, 48), 0.6, 0, 0.0, 1e-4),
+    ((16, 16, 16, 32), 0.5, 0, 0.0, 1e-2, 60, 20),
+    ((16, 16, 16, 32), 0.5, 0, 1.91, 1e-2, 60, 20),
+    ((8, 8, 8, 16), 0.3, 0, 0.0, 1e-3, 60, 20),
+    ((8, 8, 8, 16), 0.6, 0, 0.0, 1e-3, 60, 20),
+    ((24, 24, 24, 48), 0.5, 0, 0.0, 5e-3, 60, 20),
+    ((16, 16, 16, 32), 0.3, 0, 0.0, 1e-3, 60, 20),
+    ((16, 16, 16, 32), 0.6, 0, 0.0, 1e-3, 60, 20),
+    ((32, 32, 32, 64), 0.6, 0, 0.0, 1e-3, 48, 16),
+    ((24, 24, 24, 48), 0.3, 0, 0.0, 1e-3, 60, 20),
+    ((24, 24, 24, 48), 0.6, 0, 0.0, 1e-3, 60, 20),
 ]
-M, K = 60, 20
+NEV = 6
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default=None)
-    ap.add_argument("--max-matvecs", type=int, default=8000)
+    ap.add_argument("--max-restarts", type=int, default=200)
     args = ap.parse_args()
     data = {}
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    for dims, eps, seed, csw, tol in FIELDS:
-        k = fg.edge_key(dims, eps, seed, csw)
-        if args.only and args.only != k:
+    for dims, eps, seed, csw, delta, m, k in FIELDS:
+        key = fg.edge_key(dims, eps, seed, csw)
+        if args.only and args.only != key:
             continue
-        old = data.get(k, {})
-        if old.get("method") == "krylov_schur" and old.get("tol") == tol and old.get("converged"):
+        old = data.get(key, {})
+        if old.get("method") == "harmonic_ritz" and old.get("delta_ref") == delta and old.get("converged"):
             continue
         t0 = time.time()
         U = fg.gauge_field(dims, eps, seed)
         A = oracle.clover(U, dims, csw) if csw else None
+        V = fg.volume(dims)
 
-        def log(restart, mv, theta, res):
-            print(f"{k} restart {restart} matvecs {mv} theta {theta.real:.9f}{theta.imag:+.6f}i residual {res:.3e} "
-                  f"{time.time() - t0:.0f}s", flush=True)
+        def op(m0):
+            return lambda v: oracle.dw(U, np.asarray(v).reshape(V, 4, 3), dims, m0, A=A).reshape(-1)
 
-        max_restarts = max(1, (args.max_matvecs - M) // (M - K) + 1)
-        _, theta, res, mv, secs = oracle.tune_m0_schur(U, dims, 0.0, m=M, k=K, tol=tol, clov=A,
-                                                       max_restarts=max_restarts, log=log)
-        data[k] = {"dims": list(dims), "eps": eps, "seed": seed, "method": "krylov_schur", "m": M, "k": K,
-                   "tol": tol, "matvecs": mv, "converged": bool(res < tol),
-                   "edge_re": float(theta.real), "edge_im": float(theta.imag), "ritz_residual": float(res),
-                   "seconds": round(time.time() - t0, 1)}
+        e0 = old.get("edge_re")
+        if e0 is None:
+            theta, _, _ = oracle.krylov_schur_edge(op(0.0), 12 * V, 60, 20, max_restarts=7, tol=0.0)
+            e0 = float(theta.real)
+        m1 = delta - e0
+
+        def log(restart, mv, th, res):
+            print(f"{key} restart {restart} matvecs {mv} nearest "
+                  + " ".join(f"{t.real:+.6f}{t.imag:+.6f}i({r:.1e})" for t, r in zip(th, res))
+                  + f" {time.time() - t0:.0f}s", flush=True)
+
+        theta, res, mv = oracle.harmonic_ritz_nearest(op(m1), 12 * V, m=m, k=k, max_restarts=args.max_restarts,
+                                                      tol=delta / 100, nev=NEV, log=log)
+        edge = float(theta.real.min()) - m1
+        m0 = delta - edge
+        at_m0 = theta + (m0 - m1)
+        lead = int(np.argmin(theta.real))
+        data[key] = {"dims": list(dims), "eps": eps, "seed": seed, "method": "harmonic_ritz", "m": m, "k": k,
+                     "delta_ref": delta, "tol": delta / 100, "matvecs": mv, "converged": bool(res.max() < delta / 100),
+                     "edge_re": edge, "edge_im": float(theta[lead].imag), "start_edge_re": e0,
+                     "m0_ref": m0, "min_abs_eig_at_m0_ref": float(np.abs(at_m0).min()),
+                     "nearest_at_m0_ref": [[float(t.real), float(t.imag), float(r)] for t, r in zip(at_m0, res)],
+                     "seconds": round(time.time() - t0, 1)}
         if csw:
-            data[k]["csw"] = csw
-        print(k, data[k], flush=True)
+            data[key]["csw"] = csw
+        print(key, data[key], flush=True)
         with open(OUT + ".tmp", "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
         os.replace(OUT + ".tmp", OUT)

@@ -59,7 +59,7 @@ class dw_request(ctypes.Structure):
 class dw_server_status(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
                 ("running", ctypes.c_int), ("queued", ctypes.c_int), ("completed", ctypes.c_longlong),
-                ("reused", ctypes.c_longlong)]
+                ("reused", ctypes.c_longlong), ("peak_running", ctypes.c_int)]
 
 
 class dw_kernel_stat(ctypes.Structure):
@@ -80,6 +80,8 @@ _SIGS = {
     "dw_default_params": ([ctypes.POINTER(dw_solver_params)], None),
     "fgmresdr_solve": ([_P, _P, _P, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_stats)], _I),
     "dw_last_error": ([], ctypes.c_char_p),
+    "dw_cancel": ([_P], _I),
+    "dw_debug_basis": ([_P, _I, _P, _P, _P, _I, ctypes.POINTER(_I)], _I),
     "dw_profile": ([_P, _I], _I),
     "dw_kernel_launches": ([], ctypes.c_longlong),
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
@@ -182,13 +184,28 @@ def dw_default_params(**overrides) -> dw_solver_params:
     return P
 
 
-def fgmresdr_solve(ctx, b, x, params: dw_solver_params, allow_notconv: bool = False) -> dw_stats:
+def fgmresdr_solve(ctx, b, x, params: dw_solver_params, allow_notconv: bool = False,
+                   allow_cancelled: bool = False) -> dw_stats:
     S = dw_stats()
     allow = (DW_OK, DW_ENOTCONV) if allow_notconv else (DW_OK,)
+    if allow_cancelled:
+        allow = allow + (DW_ECANCELLED,)
     rc = _lib.fgmresdr_solve(ctx, _ptr(b), _ptr(x), ctypes.byref(params), ctypes.byref(S))
     _check(rc, "fgmresdr_solve", allow)
     S.status = rc
     return S
+
+
+def dw_cancel(ctx) -> None:
+    _check(_lib.dw_cancel(ctx), "dw_cancel")
+
+
+def dw_debug_basis(ctx, rhs: int, V_out=None, Z_out=None, H_out=None, max_cols: int = 64) -> int:
+    """Copies the last cycle's bases of rhs (see include/dwsolve.h); returns the column count m'."""
+    n = _I(0)
+    _check(_lib.dw_debug_basis(ctx, int(rhs), _ptr(V_out), _ptr(Z_out), _ptr(H_out), int(max_cols), ctypes.byref(n)),
+           "dw_debug_basis")
+    return n.value
 
 
 def dw_kernel_launches() -> int:

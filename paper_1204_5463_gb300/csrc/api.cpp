@@ -353,6 +353,28 @@ void dw_default_params(dw_solver_params* P) {
 }
 
 int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S) {
+    if (!ctx) return fail(DW_EINVAL, "null argument");
+    ctx->cancel.store(0);  // a cancel issued before this solve started does not apply to it
+    return solve_checked(ctx, b, x, P, S, &ctx->cancel);
+}
+
+int dw_cancel(dw_ctx* ctx) {
+    if (!ctx) return fail(DW_EINVAL, "null context");
+    ctx->cancel.store(1);
+    return DW_OK;
+}
+
+int dw_debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols) {
+    if (!ctx || !ncols) return fail(DW_EINVAL, "null argument");
+    return debug_basis(ctx, rhs, V_out, Z_out, H_out, max_cols, ncols);
+}
+
+}  // extern "C"
+
+namespace dwk {
+
+int solve_checked(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S,
+                  const std::atomic<int>* cancel) {
     if (!ctx || !b || !x || !P) return fail(DW_EINVAL, "null argument");
     if (P->m < 1 || P->m > 63) return fail(DW_EINVAL, "m must be in 1..63");
     if (P->k < 0 || P->k >= P->m || P->k > 16) return fail(DW_EINVAL, "k must satisfy 0 <= k < m and k <= 16");
@@ -368,8 +390,12 @@ int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_para
     if (P->outer_prec == DW_F32 && (P->sap_prec == DW_F64 || P->matvec_prec != DW_F32))
         return fail(DW_EINVAL, "an FP32 Arnoldi basis needs a 32- or 16-bit SAP and an FP32 matvec");
     if (!(P->clean_restart_t > 1.0)) return fail(DW_EINVAL, "clean_restart_t must be > 1");
-    return solve(ctx, b, x, P, S);
+    return solve(ctx, b, x, P, S, cancel);
 }
+
+}  // namespace dwk
+
+extern "C" {
 
 int dw_profile(dw_ctx* ctx, int enable) {
     if (!ctx) return fail(DW_EINVAL, "null context");

@@ -18,35 +18,42 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// canonical FP64 -> internal layout, times scale[r] (in FP64, before rounding)
+// when a per-rhs scale is given
 template <int P>
 __global__ void __launch_bounds__(kThreads) to_internal_kernel(const double* __restrict__ canon, char* out,
-                                                               long long V, long long out_rs) {
+                                                               long long V, long long out_rs,
+                                                               const double* __restrict__ scale) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (s >= V) return;
     typedef typename real_of<P>::type C;
+    const double f = scale ? scale[r] : 1.0;
     const double2* src = reinterpret_cast<const double2*>(canon) + ((long long)r * V + s) * 12;
     cx<C> v[12];
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
         double2 t = src[c];
-        v[c] = mk<C>((C)t.x, (C)t.y);
+        v[c] = mk<C>((C)(t.x * f), (C)(t.y * f));
     }
     store_spinor<P, C>(out + r * out_rs, V, s, v);
 }
 
+// internal layout -> canonical FP64, times scale[r] when given
 template <int P>
 __global__ void __launch_bounds__(kThreads) from_internal_kernel(const char* in, double* __restrict__ canon,
-                                                                 long long V, long long in_rs) {
+                                                                 long long V, long long in_rs,
+                                                                 const double* __restrict__ scale) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (s >= V) return;
     typedef typename real_of<P>::type C;
+    const double f = scale ? scale[r] : 1.0;
     cx<C> v[12];
     load_spinor<P, C>(in + r * in_rs, V, s, v);
     double2* dst = reinterpret_cast<double2*>(canon) + ((long long)r * V + s) * 12;
 #pragma unroll
-    for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)v[c].re, (double)v[c].im);
+    for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)v[c].re * f, (double)v[c].im * f);
 }
 
 template <int P>
@@ -205,30 +212,32 @@ int dw_dispatch_sub(const Geom& g, double m0, FieldRef in, FieldRef out, const c
 
 }  // namespace
 
-int launch_to_internal(int prec, const double* canon, char* out, long long V, int nrhs, cudaStream_t st) {
+int launch_to_internal(int prec, const double* canon, char* out, long long V, int nrhs, cudaStream_t st,
+                       const double* scale) {
     const long long rs = spinor_bytes(prec, V);
     dim3 grid = site_grid(V, nrhs);
     switch (prec) {
-        case P64: to_internal_kernel<P64><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
-        case P32: to_internal_kernel<P32><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
-        case P16: to_internal_kernel<P16><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
-        case PB16: to_internal_kernel<PB16><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
-        case PDF: to_internal_kernel<PDF><<<grid, kThreads, 0, st>>>(canon, out, V, rs); break;
+        case P64: to_internal_kernel<P64><<<grid, kThreads, 0, st>>>(canon, out, V, rs, scale); break;
+        case P32: to_internal_kernel<P32><<<grid, kThreads, 0, st>>>(canon, out, V, rs, scale); break;
+        case P16: to_internal_kernel<P16><<<grid, kThreads, 0, st>>>(canon, out, V, rs, scale); break;
+        case PB16: to_internal_kernel<PB16><<<grid, kThreads, 0, st>>>(canon, out, V, rs, scale); break;
+        case PDF: to_internal_kernel<PDF><<<grid, kThreads, 0, st>>>(canon, out, V, rs, scale); break;
         default: return fail(DW_EINVAL, "bad precision");
     }
     DW_LAUNCH_CHECK();
     return DW_OK;
 }
 
-int launch_from_internal(int prec, const char* in, double* canon, long long V, int nrhs, cudaStream_t st) {
+int launch_from_internal(int prec, const char* in, double* canon, long long V, int nrhs, cudaStream_t st,
+                         const double* scale) {
     const long long rs = spinor_bytes(prec, V);
     dim3 grid = site_grid(V, nrhs);
     switch (prec) {
-        case P64: from_internal_kernel<P64><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
-        case P32: from_internal_kernel<P32><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
-        case P16: from_internal_kernel<P16><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
-        case PB16: from_internal_kernel<PB16><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
-        case PDF: from_internal_kernel<PDF><<<grid, kThreads, 0, st>>>(in, canon, V, rs); break;
+        case P64: from_internal_kernel<P64><<<grid, kThreads, 0, st>>>(in, canon, V, rs, scale); break;
+        case P32: from_internal_kernel<P32><<<grid, kThreads, 0, st>>>(in, canon, V, rs, scale); break;
+        case P16: from_internal_kernel<P16><<<grid, kThreads, 0, st>>>(in, canon, V, rs, scale); break;
+        case PB16: from_internal_kernel<PB16><<<grid, kThreads, 0, st>>>(in, canon, V, rs, scale); break;
+        case PDF: from_internal_kernel<PDF><<<grid, kThreads, 0, st>>>(in, canon, V, rs, scale); break;
         default: return fail(DW_EINVAL, "bad precision");
     }
     DW_LAUNCH_CHECK();

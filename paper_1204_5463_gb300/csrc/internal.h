@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <complex>
 #include <string>
 #include <vector>
@@ -143,6 +145,7 @@ struct dw_ctx {
     dwk::DevBuf Uimg[4];            // SAP links per domain as shared-memory images (per storage precision)
     int Uimg_threads[4] = {0, 0, 0, 0};  // CTA size the image was packed for (0: none)
     dwk::HostFlag sap_err;          // set by a SAP sweep whose link copy did not complete
+    std::atomic<int> cancel{0};     // set by dw_cancel; the running solve stops before its next step
     const dwk::ClovRef* clover() const { return csw != 0.0 ? &clov : nullptr; }
 };
 
@@ -152,8 +155,12 @@ namespace dwk {
 int gauge_for(dw_ctx* ctx, int prec, const char** out);
 
 // ----- dw.cu ---------------------------------------------------------------
-int launch_to_internal(int prec, const double* canon, char* out, long long V, int nrhs, cudaStream_t st);
-int launch_from_internal(int prec, const char* in, double* canon, long long V, int nrhs, cudaStream_t st);
+// canonical FP64 <-> internal layout of nrhs fields; scale (device, one double
+// per rhs, may be null) multiplies every value on the way
+int launch_to_internal(int prec, const double* canon, char* out, long long V, int nrhs, cudaStream_t st,
+                       const double* scale = nullptr);
+int launch_from_internal(int prec, const char* in, double* canon, long long V, int nrhs, cudaStream_t st,
+                         const double* scale = nullptr);
 int launch_gauge_convert(int prec, const double* Ucanon, char* out, long long V, cudaStream_t st);
 int launch_link_convert(int prec, const char* U64, char* out, long long V, cudaStream_t st);
 
@@ -232,6 +239,13 @@ int launch_zero(void* p, size_t bytes, cudaStream_t st);
 int blas_nblk(long long n);
 
 // ----- solver.cpp ----------------------------------------------------------
-int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S);
+// validated solve; it stops with DW_ECANCELLED before an Arnoldi step once
+// *cancel is non-zero (cancel may be null)
+int solve_checked(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S,
+                  const std::atomic<int>* cancel);
+int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S,
+          const std::atomic<int>* cancel);
+// the basis of the last cycle of the last solve on ctx (see dw_debug_basis)
+int debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols);
 
 }  // namespace dwk

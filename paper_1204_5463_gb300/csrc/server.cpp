@@ -29,6 +29,7 @@ struct Req {
     int state = 0;  // 0 queued, 1 running, 2 done
     int status = DW_OK;
     bool cancelled = false;
+    std::atomic<int> stop{0};  // set by dw_server_cancel while running: the solve stops before its next step
     dw_stats stats{};
     clk::time_point t_submit, t_start, t_done;
 };
@@ -56,7 +57,7 @@ struct dw_server {
     std::deque<uint64_t> queue;
     std::map<uint64_t, Req> reqs;
     size_t in_use = 0, peak = 0;
-    int running = 0;
+    int running = 0, peak_running = 0;
     long long completed = 0, reused = 0;
     uint64_t next_id = 1;
     bool stop = false;
@@ -133,9 +134,10 @@ void run_request(dw_server* s, uint64_t id) {
     if (rc == DW_OK) {
         dw_solver_params P = rq->r.params;
         P.host_buffers = 1;
-        rc = fgmresdr_solve(ctx, rq->r.b, rq->r.x, &P, &S);
+        rc = dwk::solve_checked(ctx, rq->r.b, rq->r.x, &P, &S, &rq->stop);
     }
-    const bool keep = ctx && (rc == DW_OK || rc == DW_ENOTCONV);
+    // a cancelled solve stopped between two steps: its context is consistent
+    const bool keep = ctx && (rc == DW_OK || rc == DW_ENOTCONV || rc == DW_ECANCELLED);
     if (!keep) {
         if (ctx) dw_destroy(ctx);
         if (st) cudaStreamDestroy(st);
@@ -220,6 +222,7 @@ void worker(dw_server* s) {
             s->in_use += r.bytes;
             if (s->in_use > s->peak) s->peak = s->in_use;
             s->running++;
+            if (s->running > s->peak_running) s->peak_running = s->running;
         }
         run_request(s, id);
     }
@@ -313,7 +316,13 @@ int dw_server_cancel(dw_server* s, uint64_t id) {
             s->cv_done.notify_all();
             return DW_OK;
         }
-    return fail(DW_EINVAL, "request is not queued (running, finished or unknown)");
+    auto it = s->reqs.find(id);
+    if (it != s->reqs.end() && it->second.state == 1) {
+        // running: its solve returns DW_ECANCELLED before its next Arnoldi step
+        it->second.stop.store(1);
+        return DW_OK;
+    }
+    return fail(DW_EINVAL, "request is finished or unknown");
 }
 
 int dw_server_info(dw_server* s, dw_server_status* out) {
@@ -326,6 +335,7 @@ int dw_server_info(dw_server* s, dw_server_status* out) {
     out->queued = (int)s->queue.size();
     out->completed = s->completed;
     out->reused = s->reused;
+    out->peak_running = s->peak_running;
     return DW_OK;
 }
 

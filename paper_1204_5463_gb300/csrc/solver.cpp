@@ -121,7 +121,7 @@ struct Solver {
     }
 
     int setup();
-    int run(const double* b_user, double* x_user, dw_stats* S);
+    int run(const double* b_user, double* x_user, dw_stats* S, const std::atomic<int>* cancel);
     int step();
     int cycle_end(int r);
     int start_plain(int r);
@@ -136,7 +136,13 @@ struct Solver {
 
 // Workspace kept by the context between solves (grown on demand).
 struct Workspace {
-    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, norm2, scal, jtab, nz, canon, cnt;
+    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, norm2, scal, jtab, nz, canon, cnt, bscale;
+    // the last solve's bases as dw_debug_basis reads them: formats, sizes and,
+    // per rhs, the columns and the (m+1) x m Hessenberg-like matrix of its last cycle
+    int last_nrhs = 0, last_m = 0, last_vp = -1, last_zp = -1;
+    long long last_fv = 0, last_zb = 0;
+    std::vector<int> last_mm;
+    std::vector<std::vector<zd>> last_H;
     double2* dots_h = nullptr;
     double* norm2_h = nullptr;
     int* jtab_h = nullptr;
@@ -161,7 +167,7 @@ static Workspace* workspace_of(dw_ctx* ctx) {
             for (DevBuf* b : {&ctx->ws->V, &ctx->ws->Z, &ctx->ws->x, &ctx->ws->b, &ctx->ws->r, &ctx->ws->vlow,
                               &ctx->ws->zscr, &ctx->ws->rlow, &ctx->ws->zsap, &ctx->ws->partial, &ctx->ws->dots, &ctx->ws->Q, &ctx->ws->eta,
                               &ctx->ws->norm2, &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon,
-                              &ctx->ws->cnt})
+                              &ctx->ws->cnt, &ctx->ws->bscale})
                 b->st = ctx->stream;
     }
     return ctx->ws;
@@ -217,6 +223,7 @@ int Solver::setup() {
     if ((rc = W->scal.ensure((size_t)nrhs * sizeof(double)))) return rc;
     if ((rc = W->jtab.ensure((size_t)nrhs * sizeof(int)))) return rc;
     if ((rc = W->nz.ensure(sizeof(int)))) return rc;
+    if ((rc = W->bscale.ensure((size_t)2 * nrhs * sizeof(double)))) return rc;
     if (W->dots_h_n < (size_t)nrhs * NP) {
         if (W->dots_h) cudaFreeHost(W->dots_h);
         if (W->norm2_h) cudaFreeHost(W->norm2_h);
@@ -623,7 +630,7 @@ int Solver::step() {
     return DW_OK;
 }
 
-int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
+int Solver::run(const double* b_user, double* x_user, dw_stats* S, const std::atomic<int>* cancel) {
     int rc;
     const auto t0 = std::chrono::steady_clock::now();
     Workspace* W = workspace_of(ctx);
@@ -635,14 +642,35 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
         DW_CUDA_TRY(cudaMemcpyAsync(W->canon.p, b_user, canon_bytes, cudaMemcpyHostToDevice, st));
         b_dev = W->canon.as<double>();
     }
-    if ((rc = launch_to_internal(op, b_dev, bb, V, nrhs, st))) return rc;
+    // The system is solved for b scaled by the power of two nearest 1/||b|| (a
+    // per-rhs exponent shift, exact in every format, so results for b of
+    // moderate size are bit-identical to unscaled ones): the double-float and
+    // FP32 vectors keep FP32's exponent range, which b near 1e+-30 would
+    // otherwise leave in the squares of the norms. x is scaled back on output.
+    if ((rc = launch_norm2(P64, reinterpret_cast<const double2*>(b_dev), n, n, nrhs, partial, nblk, norm2d, st)))
+        return rc;
+    DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    if ((rc = sync())) return rc;
+    std::vector<double> bscale(2 * nrhs, 1.0);  // [0, nrhs): into the solver; [nrhs, 2 nrhs): back out
+    for (int r = 0; r < nrhs; ++r) {
+        const double bn = std::sqrt(norm2_h[r]);
+        if (bn > 0.0 && std::isfinite(bn)) {
+            int e = 0;
+            std::frexp(bn, &e);  // bn = f 2^e, f in [0.5, 1)
+            bscale[r] = std::ldexp(1.0, -e);
+            bscale[nrhs + r] = std::ldexp(1.0, e);
+        }
+    }
+    double* bscale_d = W->bscale.as<double>();
+    DW_CUDA_TRY(cudaMemcpyAsync(bscale_d, bscale.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, st));
+    if ((rc = launch_to_internal(op, b_dev, bb, V, nrhs, st, bscale_d))) return rc;
     if (P.use_x0) {
         if (P.host_buffers) {
             if ((rc = sync())) return rc;
             DW_CUDA_TRY(cudaMemcpyAsync(W->canon.p, x_user, canon_bytes, cudaMemcpyHostToDevice, st));
             x_dev = W->canon.as<double>();
         }
-        if ((rc = launch_to_internal(op, x_dev, xb, V, nrhs, st))) return rc;
+        if ((rc = launch_to_internal(op, x_dev, xb, V, nrhs, st, bscale_d))) return rc;
         FieldRef in{xb, fb, 0, 0}, out{rb, fb, 0, 0}, sub{bb, fb, 0, 0};
         if ((rc = launch_dw(op, op, op, g, ctx->m0, in, out, U64, nullptr, nrhs, &sub, st, ctx->clover())))
             return rc;
@@ -672,25 +700,44 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
             return rc;
         }
     }
+    bool cancelled = false;
     for (;;) {
         bool any = false;
         for (auto& s : R) any |= !s.done;
         if (!any) break;
+        if (cancel && cancel->load(std::memory_order_relaxed)) {
+            cancelled = true;
+            break;
+        }
         if ((rc = step())) return rc;
     }
     // result back to the caller's layout
     if (P.host_buffers) {
-        if ((rc = launch_from_internal(op, xb, W->canon.as<double>(), V, nrhs, st))) return rc;
+        if ((rc = launch_from_internal(op, xb, W->canon.as<double>(), V, nrhs, st, bscale_d + nrhs))) return rc;
         DW_CUDA_TRY(cudaMemcpyAsync(x_user, W->canon.p, canon_bytes, cudaMemcpyDeviceToHost, st));
     } else {
-        if ((rc = launch_from_internal(op, xb, x_user, V, nrhs, st))) return rc;
+        if ((rc = launch_from_internal(op, xb, x_user, V, nrhs, st, bscale_d + nrhs))) return rc;
     }
     if ((rc = sync())) return rc;
+    // keep the last cycle of every rhs for dw_debug_basis
+    W->last_nrhs = nrhs;
+    W->last_m = m;
+    W->last_vp = vp;
+    W->last_zp = zp;
+    W->last_fv = fv;
+    W->last_zb = zb;
+    W->last_mm.assign(nrhs, 0);
+    W->last_H.assign(nrhs, std::vector<zd>());
+    for (int r = 0; r < nrhs; ++r) {
+        W->last_mm[r] = (R[r].j < 0) ? R[r].mm : 0;  // a cycle stopped mid-way has no consistent basis
+        W->last_H[r] = R[r].H;
+    }
     int status = DW_OK, conv = 0;
     for (auto& s : R) {
         conv += s.converged;
         if (s.status != DW_OK && status == DW_OK) status = s.status;
     }
+    if (cancelled && status == DW_OK) status = DW_ECANCELLED;
     if (S) {
         std::memset(S, 0, sizeof(*S));
         for (int r = 0; r < nrhs; ++r) {
@@ -705,18 +752,56 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S) {
         S->time_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     if (status != DW_OK)
-        return fail(status, status == DW_ENOTCONV ? "iteration limit reached before the tolerance"
-                                                  : "non-finite values in the Krylov process");
+        return fail(status, status == DW_ENOTCONV    ? "iteration limit reached before the tolerance"
+                            : status == DW_ECANCELLED ? "solve cancelled"
+                                                      : "non-finite values in the Krylov process");
     return DW_OK;
 }
 
 }  // namespace
 
-int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S) {
+int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S,
+          const std::atomic<int>* cancel) {
     Solver s(ctx, *P);
     int rc = s.setup();
     if (rc) return rc;
-    return s.run(b, x, S);
+    return s.run(b, x, S, cancel);
+}
+
+int debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols) {
+    Workspace* W = ctx->ws;
+    if (!W || W->last_nrhs == 0) return fail(DW_EINVAL, "no solve has run on this context");
+    if (rhs < 0 || rhs >= W->last_nrhs) return fail(DW_EINVAL, "rhs out of range");
+    const int mm = W->last_mm[rhs];
+    *ncols = mm;
+    if (mm == 0) return DW_OK;
+    if (max_cols < mm) return fail(DW_EINVAL, "max_cols is smaller than the basis");
+    const long long V = ctx->g.V;
+    const int m = W->last_m;
+    cudaStream_t st = ctx->stream;
+    int rc;
+    if (V_out) {
+        const char* Vr = W->V.as<char>() + (long long)rhs * (m + 1) * W->last_fv;
+        for (int i = 0; i <= mm; ++i)
+            if ((rc = launch_from_internal(W->last_vp, Vr + i * W->last_fv, V_out + (long long)i * 24 * V, V, 1, st)))
+                return rc;
+    }
+    if (Z_out) {
+        const char* Zr = W->Z.as<char>() + (long long)rhs * m * W->last_zb;
+        for (int i = 0; i < mm; ++i)
+            if ((rc = launch_from_internal(W->last_zp, Zr + i * W->last_zb, Z_out + (long long)i * 24 * V, V, 1, st)))
+                return rc;
+    }
+    if (H_out) {
+        const std::vector<zd>& H = W->last_H[rhs];
+        for (int i = 0; i <= mm; ++i)
+            for (int j = 0; j < mm; ++j) {
+                H_out[2 * ((size_t)i * mm + j)] = H[(size_t)i * m + j].real();
+                H_out[2 * ((size_t)i * mm + j) + 1] = H[(size_t)i * m + j].imag();
+            }
+    }
+    DW_CUDA_TRY(cudaStreamSynchronize(st));
+    return DW_OK;
 }
 
 }  // namespace dwk

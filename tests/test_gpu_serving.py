@@ -64,6 +64,8 @@ def test_server_results_equal_alone_and_in_mix(dw):
         info = dw.dw_server_info(srv)
         assert info["completed"] == len(reqs) and info["running"] == 0
         assert info["in_use_bytes"] <= info["budget_bytes"]  # idle cached contexts only
+        # the requests really overlapped: several were solving at the same time
+        assert info["peak_running"] >= 2
     finally:
         dw.dw_server_destroy(srv)
     for q, x in zip(reqs, xs):
@@ -147,5 +149,42 @@ def test_server_reuses_resident_gauge_field(dw):
             assert status == dw.DW_OK
         assert dw.dw_server_info(srv)["reused"] == 1
         assert np.array_equal(xs[0], xs[1])
+    finally:
+        dw.dw_server_destroy(srv)
+
+
+def test_server_cancels_a_running_request(dw):
+    """A request that would run for long (an unreachable tolerance) is
+    cancelled while it solves: it stops between two Arnoldi steps with
+    DW_ECANCELLED, the server stays usable, and the next request on the same
+    gauge field (taking over the cancelled request's context) is exact."""
+    import time
+
+    q = _requests()[1]
+    srv = dw.dw_server_create(8 << 30, 1)
+    try:
+        x = np.zeros_like(q["b"])
+        # restarted FGMRES (no eigenproblem to break down at the rounding floor);
+        # 2000 cycles bound the request to seconds should the cancel be missed
+        P = dw.dw_default_params(m=16, k=0, tol=1e-30, max_cycles=2000, sap_cycles=3, mr_steps=3,
+                                 nrhs=q["nrhs"])
+        r = dw.make_request(q["dims"], q["block"], q["m0"], q["U"], q["b"], x, P)
+        rid = dw.dw_server_submit(srv, r)
+        t0 = time.time()
+        while dw.dw_server_info(srv)["running"] == 0 and time.time() - t0 < 60:
+            time.sleep(0.01)
+        time.sleep(0.2)  # a few hundred steps
+        dw.dw_server_cancel(srv, rid)
+        status, S, lat = dw.dw_server_wait(srv, rid, 60)
+        assert status == dw.DW_ECANCELLED
+        assert S.iterations > 0
+        with pytest.raises(dw.DwError):
+            dw.dw_server_cancel(srv, rid)  # finished now
+        x2 = np.zeros_like(q["b"])
+        r2 = dw.make_request(q["dims"], q["block"], q["m0"], q["U"], q["b"], x2, _params(dw, q["nrhs"]))
+        status, _, _ = dw.dw_server_wait(srv, dw.dw_server_submit(srv, r2), 300)
+        assert status == dw.DW_OK
+        assert dw.dw_server_info(srv)["reused"] == 1
+        assert np.array_equal(x2, _alone(dw, q))
     finally:
         dw.dw_server_destroy(srv)

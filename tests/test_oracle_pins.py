@@ -476,6 +476,30 @@ def test_tuned_mass_puts_dense_spectrum_edge_at_target(how):
     assert np.abs(ev).min() >= target - 1e-9
 
 
+def test_harmonic_ritz_nearest_finds_the_eigenvalues_nearest_the_origin():
+    """Thick-restarted harmonic Ritz extraction (Lemma 1a with the
+    eigenvector residual as the extra restart vector) on D_{m0} just above the
+    critical mass: the values are the dense spectrum's eigenvalues of smallest
+    modulus, and each reported residual is ||D u - theta u|| of its vector."""
+    dims = (2, 2, 4, 4)
+    U = fg.gauge_field(dims, 0.5, seed=0)
+    ev0 = np.linalg.eigvals(_dense(U, dims, 0.0))
+    m0 = 0.02 - ev0.real.min()
+    A = _dense(U, dims, m0)
+    n = A.shape[0]
+    theta, res, mv, X = oracle.harmonic_ritz_nearest(lambda v: A @ v, n, m=40, k=12, max_restarts=300, tol=1e-9,
+                                                     nev=4, seed=6, return_vectors=True)
+    assert mv > 40  # restarted
+    ev = np.linalg.eigvals(A)
+    near = ev[np.argsort(np.abs(ev))[:4]]
+    for t in theta:
+        assert np.abs(near - t).min() < 1e-7
+    assert abs(np.abs(theta).min() - np.abs(ev).min()) < 1e-8
+    for i in range(4):
+        assert res[i] < 1e-9
+        assert abs(np.linalg.norm(A @ X[:, i] - theta[i] * X[:, i]) - res[i]) < 1e-10
+
+
 # --------------------------------------------------------------------------- clover term
 def _abelian_field(dims, b):
     """U_{n,0} = diag(e^{i b n_1}, e^{-i b n_1}, 1), all other links 1: a uniform

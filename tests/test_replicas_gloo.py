@@ -71,7 +71,7 @@ def test_reference_arm_under_torchrun():
     env["OMP_NUM_THREADS"] = "4"
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
            "127.0.0.1", "--master-port", str(_free_port()), os.path.join(ROOT, "bench.py"), "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-iterations", "81"]
+           "--gpus", "2", "--steps", "2", "--warmup", "0", "--ref-chunk", "1"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
