@@ -254,6 +254,26 @@ typedef struct {
 int dw_autotune_block(const dw_lattice* L, const double* U, const double* b, const dw_solver_params* P,
                       void* cuda_stream, int* best_block, dw_tune_entry* results, int max_results, int* n_results);
 
+/* SAP work per preconditioner application, tuned on a fixed block: the pairs
+ * (sap_cycles, mr_steps) in {3, 4, 5, 6, 8} x {3, 4, 5, 6} are ranked by the
+ * wall time of a calibration solve P on L's block (more SAP work per step buys
+ * fewer Arnoldi steps and Gram-Schmidt passes, so the best pair depends on
+ * the relative cost of a sweep, e.g. on the storage precision and the number
+ * of right-hand sides). The paper fixes these (Sec. 6: 5 MR steps; 8 to 24
+ * SAP cycles); this searches them. Writes the fastest converged pair; with
+ * results, up to max_results timed pairs and their count. Cached per (dims,
+ * block, nrhs, precisions, m, k). Errors as dw_autotune_block. */
+typedef struct {
+    int sap_cycles, mr_steps;
+    double seconds;  /* wall time of the calibration solve (1e300 if it failed) */
+    int iterations;
+    int status;
+} dw_tune_sap_entry;
+
+int dw_autotune_sap(const dw_lattice* L, const double* U, const double* b, const dw_solver_params* P,
+                    void* cuda_stream, int* best_cycles, int* best_mr, dw_tune_sap_entry* results, int max_results,
+                    int* n_results);
+
 /* ---- allocation-free operator ----------------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that
  * cannot call cudaMalloc (code inside a pre-reserved memory pool, allocators

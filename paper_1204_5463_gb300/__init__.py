@@ -51,6 +51,11 @@ class dw_tune_entry(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class dw_tune_sap_entry(ctypes.Structure):
+    _fields_ = [("sap_cycles", ctypes.c_int), ("mr_steps", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("status", ctypes.c_int)]
+
+
 class dw_request(ctypes.Structure):
     _fields_ = [("lattice", dw_lattice), ("U", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("params", dw_solver_params)]
@@ -87,6 +92,9 @@ _SIGS = {
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
     "dw_autotune_block": ([ctypes.POINTER(dw_lattice), _P, _P, ctypes.POINTER(dw_solver_params), _P,
                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dw_tune_entry), _I, ctypes.POINTER(_I)], _I),
+    "dw_autotune_sap": ([ctypes.POINTER(dw_lattice), _P, _P, ctypes.POINTER(dw_solver_params), _P,
+                         ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(dw_tune_sap_entry), _I,
+                         ctypes.POINTER(_I)], _I),
     "dw_apply_f32_noalloc": ([ctypes.POINTER(ctypes.c_int), ctypes.c_double, _P, _P, _P, _P], _I),
     "dw_request_bytes": ([ctypes.POINTER(dw_request)], ctypes.c_size_t),
     "dw_server_create": ([ctypes.c_size_t, _I, ctypes.POINTER(_P)], _I),
@@ -236,6 +244,21 @@ def dw_autotune_block(dims, m0: float, U, b, params: dw_solver_params, stream=No
     table = [(tuple(res[i].block), res[i].seconds, res[i].iterations, res[i].status)
              for i in range(min(n.value, 256))] if with_results else []
     return tuple(best), table
+
+
+def dw_autotune_sap(dims, block, m0: float, U, b, params: dw_solver_params, stream=None, with_results: bool = True):
+    """Best (sap_cycles, mr_steps) on this block by calibration-solve time;
+    returns ((cycles, mr), [(cycles, mr, seconds, iterations, status)])."""
+    L = dw_lattice((ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(*block), float(m0))
+    c, m = _I(), _I()
+    res = (dw_tune_sap_entry * 64)() if with_results else None
+    n = _I(0)
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(_lib.dw_autotune_sap(ctypes.byref(L), _ptr(U), _ptr(b), ctypes.byref(params), s, ctypes.byref(c),
+                                ctypes.byref(m), res, 64 if with_results else 0, ctypes.byref(n)), "dw_autotune_sap")
+    table = [(res[i].sap_cycles, res[i].mr_steps, res[i].seconds, res[i].iterations, res[i].status)
+             for i in range(min(n.value, 64))] if with_results else []
+    return (c.value, m.value), table
 
 
 def dw_apply_f32_noalloc(dims, m0: float, U, inp, out, stream=None) -> None:

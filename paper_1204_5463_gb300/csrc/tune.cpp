@@ -23,6 +23,8 @@ using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int>;
 
 std::mutex g_mu;
 std::map<Key, std::vector<int>> g_cache;
+std::map<Key, std::vector<int>> g_sap_cache;  // (cycles, mr) per lattice, block in the key's place of the
+                                             // SAP parameters
 
 Key make_key(const dw_lattice* L, const dw_solver_params* P) {
     return Key(L->dims[0], L->dims[1], L->dims[2], L->dims[3], P->nrhs, (int)P->sap_prec, (int)P->outer_prec, P->m,
@@ -130,5 +132,86 @@ extern "C" int dw_autotune_block(const dw_lattice* L, const double* U, const dou
     if (best >= 1e300) return fail(DW_ENOTCONV, "no candidate block converged");
     std::lock_guard<std::mutex> lock(g_mu);
     g_cache[key] = std::vector<int>(best_block, best_block + 4);
+    return DW_OK;
+}
+
+// SAP work per preconditioner application: more cycles and MR steps make each
+// Arnoldi step dearer and (up to a point) the solve shorter, and the balance
+// moves with the cost of a sweep relative to the Gram-Schmidt passes (e.g.
+// many right-hand sides in 16-bit storage make sweeps cheap per rhs). The
+// pairs of a small grid are ranked by the time to solution of a calibration
+// solve on the caller's block.
+extern "C" int dw_autotune_sap(const dw_lattice* L, const double* U, const double* b, const dw_solver_params* P,
+                               void* cuda_stream, int* best_cycles, int* best_mr, dw_tune_sap_entry* results,
+                               int max_results, int* n_results) {
+    if (!L || !U || !b || !P || !best_cycles || !best_mr) return fail(DW_EINVAL, "null argument");
+    long long V = 0;
+    if (!lattice_volume(L->dims, kMaxSites, &V)) return fail(DW_EINVAL, "bad lattice extents");
+    const Key key(L->dims[0], L->dims[1], L->dims[2], L->dims[3], P->nrhs, (int)P->sap_prec, (int)P->outer_prec,
+                  P->m, P->k, L->block[0] + 1000 * L->block[1], L->block[2] + 1000 * L->block[3]);
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = g_sap_cache.find(key);
+        if (it != g_sap_cache.end() && !results) {
+            *best_cycles = it->second[0];
+            *best_mr = it->second[1];
+            if (n_results) *n_results = 0;
+            return DW_OK;
+        }
+    }
+    static const int kCycles[] = {3, 4, 5, 6, 8};
+    static const int kMr[] = {3, 4, 5, 6};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    DevBuf x;
+    x.st = st;
+    int rc = x.ensure((size_t)P->nrhs * 24 * V * sizeof(double));
+    if (rc) return rc;
+    dw_ctx* ctx = nullptr;
+    if ((rc = dw_create(L, cuda_stream, &ctx))) return rc;
+    if ((rc = dw_set_gauge(ctx, U, 1))) {
+        dw_destroy(ctx);
+        return rc;
+    }
+    dw_solver_params Q = *P;
+    Q.host_buffers = 0;
+    Q.use_x0 = 0;
+    {  // warm-up: workspace, link copies and images for this block
+        dw_stats S{};
+        fgmresdr_solve(ctx, b, x.as<double>(), &Q, &S);
+    }
+    double best = 1e300;
+    int cnt = 0;
+    for (int c : kCycles)
+        for (int mr : kMr) {
+            Q.sap_cycles = c;
+            Q.mr_steps = mr;
+            dw_stats S{};
+            const auto t0 = std::chrono::steady_clock::now();
+            const int status = fgmresdr_solve(ctx, b, x.as<double>(), &Q, &S);
+            double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (status != DW_OK) secs = 1e300;
+            if (results && cnt < max_results) {
+                results[cnt].sap_cycles = c;
+                results[cnt].mr_steps = mr;
+                results[cnt].seconds = secs;
+                results[cnt].iterations = S.iterations;
+                results[cnt].status = status;
+            }
+            ++cnt;
+            if (secs < best) {
+                best = secs;
+                *best_cycles = c;
+                *best_mr = mr;
+            }
+            if (status == DW_ECUDA || status == DW_ETIMEOUT) {
+                dw_destroy(ctx);
+                return status;
+            }
+        }
+    dw_destroy(ctx);
+    if (n_results) *n_results = cnt;
+    if (best >= 1e300) return fail(DW_ENOTCONV, "no SAP setting converged");
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_sap_cache[key] = std::vector<int>{*best_cycles, *best_mr};
     return DW_OK;
 }

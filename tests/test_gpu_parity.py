@@ -6,10 +6,16 @@ thread blocks), plus edge cases: a 2^4 lattice (n + j == n - j), domains of
 one site in a direction, several right-hand sides per launch.
 
 Tolerances (relative, max-norm over the field unless stated):
-  D:   FP64 1e-12, FP32 1e-5, FP16 storage 5e-3, BF16 storage 3e-2
-  SAP: FP64 1e-11, FP32 1e-4 (2-norm), FP16 2e-2, BF16 1e-1 (2-norm)
-The SAP bounds follow from the unit roundoff u of the storage format times
-the growth of a few MR steps and SAP cycles (measured growth < 100 u).
+  D:   FP64 1e-12, FP32 1e-5, FP16 storage 5e-3 (the stated ones), BF16 storage
+       1e-2 (2.6 u of BF16)
+  SAP: FP64 1e-11 (max-norm); FP32 2.4e-7 = 4 u, FP16 9.8e-4 = 2 u, BF16
+       7.8e-3 = 2 u of the storage format (2-norm)
+With 16-bit storage the rounding of the stored input and output dominates
+(u = 2^-11 for FP16, 2^-8 for BF16; the FP32 arithmetic adds ~2^-24 per
+operation), so the errors sit below one u: measured on these cases D 0.73 u
+(FP16) and 0.9 u (BF16) in the max-norm, SAP 0.6 u (FP16, BF16) in the 2-norm.
+FP32 SAP accumulates FP32 rounding over its MR steps and cycles: measured
+1.4 u (2-norm), hence 4 u.
 """
 
 import numpy as np
@@ -22,8 +28,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-DW_TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3, 3: 3e-2}
-SAP_TOL = {0: 1e-11, 1: 1e-4, 2: 2e-2, 3: 1e-1}
+DW_TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3, 3: 1e-2}
+SAP_TOL = {0: 1e-11, 1: 4 * 2.0 ** -24, 2: 2 * 2.0 ** -11, 3: 2 * 2.0 ** -8}
 
 
 @pytest.fixture(scope="module")
