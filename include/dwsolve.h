@@ -255,7 +255,7 @@ int dw_autotune_block(const dw_lattice* L, const double* U, const double* b, con
                       void* cuda_stream, int* best_block, dw_tune_entry* results, int max_results, int* n_results);
 
 /* SAP work per preconditioner application, tuned on a fixed block: the pairs
- * (sap_cycles, mr_steps) in {3, 4, 5, 6, 8} x {3, 4, 5, 6} are ranked by the
+ * (sap_cycles, mr_steps) in {2, 3, 4, 5, 6, 8} x {3, 4, 5, 6, 8, 10} are ranked by the
  * wall time of a calibration solve P on L's block (more SAP work per step buys
  * fewer Arnoldi steps and Gram-Schmidt passes, so the best pair depends on
  * the relative cost of a sweep, e.g. on the storage precision and the number

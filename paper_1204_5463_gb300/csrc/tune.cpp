@@ -159,8 +159,8 @@ extern "C" int dw_autotune_sap(const dw_lattice* L, const double* U, const doubl
             return DW_OK;
         }
     }
-    static const int kCycles[] = {3, 4, 5, 6, 8};
-    static const int kMr[] = {3, 4, 5, 6};
+    static const int kCycles[] = {2, 3, 4, 5, 6, 8};
+    static const int kMr[] = {3, 4, 5, 6, 8, 10};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     DevBuf x;
     x.st = st;

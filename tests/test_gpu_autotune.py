@@ -60,8 +60,8 @@ def test_autotune_sap_picks_fastest_converged_pair():
     b = fg.gaussian_source(dims, 4)
     P = dw.dw_default_params(m=16, k=4, tol=1e-8)
     best, table = dw.dw_autotune_sap(dims, block, m0, _dev(U), _dev(b), P)
-    assert len(table) == 20
-    assert {(t[0], t[1]) for t in table} == {(c, m) for c in (3, 4, 5, 6, 8) for m in (3, 4, 5, 6)}
+    assert len(table) == 36
+    assert {(t[0], t[1]) for t in table} == {(c, m) for c in (2, 3, 4, 5, 6, 8) for m in (3, 4, 5, 6, 8, 10)}
     ok = [t for t in table if t[4] == dw.DW_OK]
     assert best == min(ok, key=lambda t: t[2])[:2]
     ctx = dw.dw_create(dims, block, m0)
