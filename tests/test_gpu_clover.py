@@ -14,8 +14,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CSW = 1.91
-DW_TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3, 3: 3e-2}
-SAP_TOL = {0: 1e-11, 1: 1e-4, 2: 2e-2}
+# the tolerances of tests/test_gpu_parity.py (derived there from the unit
+# roundoff of the storage format)
+DW_TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3, 3: 1e-2}
+SAP_TOL = {0: 1e-11, 1: 4 * 2.0 ** -24, 2: 2 * 2.0 ** -11}
 
 
 @pytest.fixture(scope="module")

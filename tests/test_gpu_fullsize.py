@@ -107,7 +107,7 @@ def test_sap_full_16x16x16x32_fp32(dw, wilson, ncyc):
         got = host(z, v.shape)
     finally:
         dw.dw_destroy(ctx)
-    assert rel2(got, ref) <= 1e-4
+    assert rel2(got, ref) <= 4 * 2.0 ** -24  # 4 u of FP32 (measured 1.4 u after 1 and 5 cycles)
 
 
 @pytest.mark.parametrize("outer", [4, 1])
