@@ -604,6 +604,18 @@ def run_workload(args, rank, world):
     elif args.workload == "sap_standalone":
         cfg = workload()
         out = sap_standalone_leg(args, cfg, _dev(fg.gauge_field(cfg["dims"], cfg["eps"], cfg["seed"])))
+    elif args.workload == "sap_sweep":
+        # the SAP sweep alone (FP32, one rhs, the benchmark's SAP settings) on
+        # the lattice of --dw-lattice: its ALU roofline where the grid fills the GPU
+        import paper_1204_5463_gb300 as dw
+
+        dims = tuple(int(v) for v in args.dw_lattice.split("x"))
+        ctx = dw.dw_create(dims, (4, 4, 4, 4), -0.6, torch.cuda.current_stream().cuda_stream)
+        dw.dw_set_gauge(ctx, _dev(fg.gauge_field(dims, 0.5, 0)), True)
+        out = {"workload": "sap_sweep", "lattice": list(dims),
+               "sap_sweep_f32": _profiled_sap(dw, torch, ctx, _dev(fg.gaussian_source(dims, 1)), 5, 4, dw.DW_F32, 1,
+                                              fg.volume(dims), (4, 4, 4, 4))}
+        dw.dw_destroy(ctx)
     elif args.workload.startswith("batched"):
         out = batched_leg(args)
     elif args.workload.startswith("mixed"):
@@ -639,7 +651,8 @@ def main():
                     help="Arnoldi basis of the served solves (f32: the single-precision scheme of Sec. 5.7)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="wilson_16x16x16x32 (default, the benchmark line), batched_24x24x24x48, mixed_32x32x32x64, "
-                         "sap_standalone (SAP as a solver around the spectral edge, 16^3x32)")
+                         "sap_standalone (SAP as a solver around the spectral edge, 16^3x32), sap_sweep (one SAP "
+                         "application alone on --dw-lattice)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--k0-cycles", type=int, default=40, help="cycle cap of the restarted FGMRES comparison")
     ap.add_argument("--sap-cycles-max", type=int, default=30, help="SAP cycles of the stand-alone SAP runs")
@@ -871,6 +884,11 @@ def main():
                 "ms_per_step": fms / args.steps, "iterations": S64.iterations, "cycles": S64.cycles,
                 "clean_restarts": S64.clean_restarts, "true_rel_res": S64.true_rel_res[0],
                 "ratio_vs_double_float": fv / value}
+        if mb:
+            # the mixed-precision batched variants against the plain solver as
+            # the workload defines it (FP32 stencil, FP64 outer vectors) as well
+            for leg in [mb] + [mb[k] for k in ("f32_basis", "tuned_sap", "tuned_sap_f32_basis") if k in mb]:
+                leg["ratio_vs_plain_fp64_outer"] = leg["value"] / fv
 
     # the clover-improved operator (c_sw = 1.91, the paper's 16^3 x 32 value)
     # on the same links, bare mass tuned to its own spectral edge

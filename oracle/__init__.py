@@ -534,7 +534,8 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
 
 
 def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts: int = 100, tol: float = 1e-6,
-                          nev: int = 4, seed: int = 0, log=None, return_vectors: bool = False):
+                          nev: int = 4, seed: int = 0, log=None, return_vectors: bool = False,
+                          near_factor: float | None = None):
     """Eigenvalues of A nearest the origin by harmonic Ritz extraction with
     thick restarts (the deflated restart of GMRES-DR without the linear system).
 
@@ -549,7 +550,8 @@ def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts:
     satisfy A V_k = V_{k+1} Hhat_k (Eqs. "G_kplus1", "tildeV_Vplus1",
     "hatHk" with the eigenvector residual in place of the linear system's).
     Stops once the nev pairs of smallest |theta| all have residual norms
-    below tol. Returns (theta[nev], residual norms[nev], matvecs), plus the
+    below tol (with near_factor: once those of them with |theta| <= near_factor
+    times the smallest |theta| do). Returns (theta[nev], residual norms[nev], matvecs), plus the
     unit vectors u (columns of an n x nev array) with return_vectors."""
     rng = np.random.default_rng(seed)
     V = np.zeros((m + 1, n), dtype=np.complex128)
@@ -579,7 +581,8 @@ def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts:
         theta, res = lam[order[:nev]], allres[order[:nev]]
         if log is not None:
             log(restart, matvecs, theta, res)
-        if res.max() < tol or restart == max_restarts - 1:
+        watch = res if near_factor is None else res[np.abs(theta) <= near_factor * np.abs(theta[0])]
+        if watch.max() < tol or restart == max_restarts - 1:
             if return_vectors:
                 Gs = G[:, order[:nev]]
                 U = V[:m].T @ (Gs / np.linalg.norm(Gs, axis=0))

@@ -409,6 +409,74 @@ __global__ void __launch_bounds__(kT) multiaxpy_kernel(VecRef Vb, VecRef w, long
     }
 }
 
+// The FP32-basis form of the multi-axpy: two complex numbers per thread and
+// vector (one 16-byte load instead of two 8-byte ones), so each thread keeps
+// twice the bytes in flight through its chain of multiply-adds; same
+// arithmetic per complex number as multiaxpy_kernel<P32>. n is even (12 per site).
+__global__ void __launch_bounds__(kT) multiaxpy_f32x2_kernel(VecRef Vb, VecRef w, long long n, const int* jtab,
+                                                            int nv_off, const double2* coef, int coef_ld,
+                                                            double2* partial, unsigned* cnt, double* fin) {
+    __shared__ float2 h[kMaxV];
+    __shared__ double red[kT / 32];
+    const int r = blockIdx.y;
+    if (jtab && jtab[r] < 0) return;
+    const int nv = rhs_nv(jtab, r, nv_off);
+    const int j = jtab ? jtab[r] : 0;
+    for (int i = threadIdx.x; i < nv; i += kT) {
+        const double2 c = coef[(long long)r * coef_ld + i];
+        h[i] = make_float2((float)-c.x, (float)-c.y);
+    }
+    __syncthreads();
+    const float4* Vr = reinterpret_cast<const float4*>(Vb.base + r * Vb.rhs_stride);
+    float4* wr = reinterpret_cast<float4*>(w.base + r * w.rhs_stride + (long long)(j + w.col_off) * w.col_stride);
+    const long long cs = Vb.col_stride;  // 16-byte units = float4 elements
+    const long long stride = (long long)gridDim.x * kT;
+    const long long n2 = n / 2;
+    float wacc = 0.f;
+    for (long long e = (long long)blockIdx.x * kT + threadIdx.x; e < n2; e += stride) {
+        float4 acc = wr[e];
+        for (int i = 0; i < nv; ++i) {
+            const float2 hi = h[i];
+            const float4 a = __ldg(&Vr[(long long)(i + Vb.col_off) * cs + e]);
+            acc.x = fmaf(hi.x, a.x, acc.x);
+            acc.x = fmaf(-hi.y, a.y, acc.x);
+            acc.y = fmaf(hi.x, a.y, acc.y);
+            acc.y = fmaf(hi.y, a.x, acc.y);
+            acc.z = fmaf(hi.x, a.z, acc.z);
+            acc.z = fmaf(-hi.y, a.w, acc.z);
+            acc.w = fmaf(hi.x, a.w, acc.w);
+            acc.w = fmaf(hi.y, a.z, acc.w);
+        }
+        wr[e] = acc;
+        wacc = fmaf(acc.x, acc.x, fmaf(acc.y, acc.y, wacc));
+        wacc = fmaf(acc.z, acc.z, fmaf(acc.w, acc.w, wacc));
+    }
+    const double wn = warp_sum((double)wacc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < kT / 32; ++q) s += red[q];
+        partial[(long long)r * gridDim.x + blockIdx.x] = make_double2(s, 0.0);
+    }
+    if (cnt) {  // the last CTA sums the partial norms in the finalize kernel's order
+        __shared__ unsigned is_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) is_last = (atomicAdd(cnt + r, 1u) == gridDim.x - 1);
+        __syncthreads();
+        if (!is_last || threadIdx.x >= 32) return;
+        __threadfence();
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(&partial[(long long)r * gridDim.x + b].x);
+        s = warp_sum(s);
+        if (threadIdx.x == 0) {
+            fin[r] = s;
+            cnt[r] = 0u;
+        }
+    }
+}
+
 // ---- v = w / ||w|| per site, optionally also written in SAP storage ----------
 template <int VP, int PS>
 __global__ void __launch_bounds__(kT) normalize_kernel(VecRef w, VecRef dst, long long V, const int* jtab,
@@ -767,6 +835,9 @@ int launch_multiaxpy(int vp, VecRef Vb, VecRef w, long long n, const int* jtab, 
     if (vp == PDF)
         multiaxpy_kernel<PDF><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial, cnt,
                                                               out_norm2);
+    else if (vp == P32 && n % 2 == 0)
+        multiaxpy_f32x2_kernel<<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial, cnt,
+                                                                out_norm2);
     else if (vp == P32)
         multiaxpy_kernel<P32><<<dim3(nblk, nrhs), kT, 0, st>>>(Vb, w, n, jtab, nv_off, coef, coef_ld, partial, cnt,
                                                               out_norm2);

@@ -410,6 +410,10 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(C) == 4) ? 2 : 1)
             SAP_LOC_HOPS(2, ls2)
             SAP_LOC_HOPS(3, ls3)
 #undef SAP_LOC_HOPS
+            // the site's own rho is read back from shared memory (where the
+            // neighbours read it) rather than kept in registers over the hops:
+            // the 24 registers go to overlapping the hops' loads
+            rho_load<C>(rsh, T, tid, rho);
             if constexpr (CLOV) clover_acc<CP, C>(clov, g.V, s, rho, acc, (C)-2);  // A rho as -2 A rho in acc
             const C half = (C)0.5;
 #pragma unroll

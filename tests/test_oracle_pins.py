@@ -498,6 +498,16 @@ def test_harmonic_ritz_nearest_finds_the_eigenvalues_nearest_the_origin():
     for i in range(4):
         assert res[i] < 1e-9
         assert abs(np.linalg.norm(A @ X[:, i] - theta[i] * X[:, i]) - res[i]) < 1e-10
+    # stopping on the values near the smallest only: those are converged and
+    # are the dense eigenvalues; the rest carry their (true) residuals
+    theta, res, _, X = oracle.harmonic_ritz_nearest(lambda v: A @ v, n, m=40, k=12, max_restarts=300, tol=1e-9,
+                                                    nev=8, seed=6, return_vectors=True, near_factor=1.5)
+    near = np.abs(theta) <= 1.5 * np.abs(theta[0])
+    assert near.sum() >= 1 and res[near].max() < 1e-9
+    for t in theta[near]:
+        assert np.abs(ev - t).min() < 1e-7
+    for i in range(8):
+        assert abs(np.linalg.norm(A @ X[:, i] - theta[i] * X[:, i]) - res[i]) < 1e-10 + 1e-7 * res[i]
 
 
 # --------------------------------------------------------------------------- clover term
