@@ -962,7 +962,7 @@ def main():
     dwbw = None if args.no_dw_bw else dw_bandwidth(peaks, dims=tuple(int(v) for v in args.dw_lattice.split("x")))
     sap16 = _profiled_sap(dw, torch, ctx, bd, cfg["sap_cycles"], cfg["mr_steps"], dw.DW_F32, 1, V, block)
     extra = {}
-    if not args.no_extra:
+    if not args.no_extra and world == 1:  # single-GPU workloads, measured at N = 1 only
         extra["sap_standalone"] = sap_standalone_leg(args, cfg, Ud)
         extra["batched_24x24x24x48"] = batched_leg(args)
         extra["mixed_32x32x32x64"] = mixed_leg(args)
