@@ -766,6 +766,8 @@ def main():
     ev1.record(stream)
     barrier()
     launches = dw.dw_kernel_launches() - launches0
+    # residual against Arnoldi steps per cycle of the last timed solve (the paper's plots)
+    history = [[h[0], h[1], h[2]] for h in dw.dw_residual_history(ctx, 0)]
     # timed region 2: the same K solves with the library's per-kernel CUDA
     # events on the solver's stream (the roofline and the kernel shares); the
     # events themselves cost wall time, so the headline comes from region 1
@@ -992,6 +994,8 @@ def main():
         "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)), "min": min(lat)},
         "iterations": iters,
         "clean_restarts": cleans,
+        "residual_history": {"columns": ["arnoldi_steps", "implicit_rel_res", "explicit_rel_res"],
+                             "cycles": history},
         "roofline": roof,
         "kernel_share": shares,
         "kernel_avg_us": avg_us,

@@ -192,6 +192,15 @@ int fgmresdr_solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_para
  * while no solve runs has no effect. Safe to call from any thread. */
 int dw_cancel(dw_ctx* ctx);
 
+/* Residual history of the last fgmresdr_solve on ctx for right-hand side rhs,
+ * the quantities the paper plots (Sec. 6: residual against the number of
+ * matrix-vector products): for each cycle end i, out[3i] = Arnoldi steps so
+ * far, out[3i+1] = the implicit (least-squares) relative residual of the
+ * cycle, out[3i+2] = the explicit ||b - D x|| / ||b|| computed after it
+ * (Sec. 5.7). *n = the number of cycle ends; at most max are written (out may
+ * be NULL to query *n). */
+int dw_residual_history(dw_ctx* ctx, int rhs, double* out, int max, int* n);
+
 /* Test and diagnosis hook (not part of the paper's method): copies the bases
  * of the last cycle of the last fgmresdr_solve on ctx for right-hand side rhs,
  * so that the flexible Arnoldi relation A Z_m = V_{m+1} Hhat_m (Eq.

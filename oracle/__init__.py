@@ -535,7 +535,7 @@ def krylov_schur_edge(apply, n: int, m: int = 60, k: int = 20, max_restarts: int
 
 def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts: int = 100, tol: float = 1e-6,
                           nev: int = 4, seed: int = 0, log=None, return_vectors: bool = False,
-                          near_factor: float | None = None):
+                          near_factor: float | None = None, stop=None):
     """Eigenvalues of A nearest the origin by harmonic Ritz extraction with
     thick restarts (the deflated restart of GMRES-DR without the linear system).
 
@@ -551,7 +551,8 @@ def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts:
     "hatHk" with the eigenvector residual in place of the linear system's).
     Stops once the nev pairs of smallest |theta| all have residual norms
     below tol (with near_factor: once those of them with |theta| <= near_factor
-    times the smallest |theta| do). Returns (theta[nev], residual norms[nev], matvecs), plus the
+    times the smallest |theta| do), or when stop() returns True after a
+    restart. Returns (theta[nev], residual norms[nev], matvecs), plus the
     unit vectors u (columns of an n x nev array) with return_vectors."""
     rng = np.random.default_rng(seed)
     V = np.zeros((m + 1, n), dtype=np.complex128)
@@ -582,7 +583,7 @@ def harmonic_ritz_nearest(apply, n: int, m: int = 60, k: int = 20, max_restarts:
         if log is not None:
             log(restart, matvecs, theta, res)
         watch = res if near_factor is None else res[np.abs(theta) <= near_factor * np.abs(theta[0])]
-        if watch.max() < tol or restart == max_restarts - 1:
+        if watch.max() < tol or restart == max_restarts - 1 or (stop is not None and stop()):
             if return_vectors:
                 Gs = G[:, order[:nev]]
                 U = V[:m].T @ (Gs / np.linalg.norm(Gs, axis=0))

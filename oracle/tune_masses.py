@@ -74,6 +74,8 @@ def main():
     ap.add_argument("--max-restarts", type=int, default=200)
     ap.add_argument("--force", action="store_true", help="recompute fields that are already stored")
     ap.add_argument("--out", default=OUT, help="file to merge the results into")
+    ap.add_argument("--max-seconds", type=float, default=None,
+                    help="stop the harmonic Ritz run after this long and store its values as not converged")
     args = ap.parse_args()
     out_path = args.out
     data = {}
@@ -115,7 +117,9 @@ def main():
                   + f" {time.time() - t0:.0f}s", flush=True)
 
         theta, res, mv = oracle.harmonic_ritz_nearest(op(m1), 12 * V, m=m, k=k, max_restarts=args.max_restarts,
-                                                      tol=delta / 10, nev=NEV, log=log, near_factor=2.0)
+                                                      tol=delta / 10, nev=NEV, log=log, near_factor=2.0,
+                                                      stop=(lambda: time.time() - t0 > args.max_seconds)
+                                                      if args.max_seconds else None)
         lead = int(np.argmin(theta.real))
         edge, edge_im = float(theta.real.min()) - m1, float(theta[lead].imag)
         if ks and ks["converged"] and ks["edge_re"] < edge:

@@ -87,6 +87,7 @@ _SIGS = {
     "dw_last_error": ([], ctypes.c_char_p),
     "dw_cancel": ([_P], _I),
     "dw_debug_basis": ([_P, _I, _P, _P, _P, _I, ctypes.POINTER(_I)], _I),
+    "dw_residual_history": ([_P, _I, _P, _I, ctypes.POINTER(_I)], _I),
     "dw_profile": ([_P, _I], _I),
     "dw_kernel_launches": ([], ctypes.c_longlong),
     "dw_profile_read": ([_P, ctypes.POINTER(dw_kernel_stat), _I, ctypes.POINTER(_I), _I], _I),
@@ -214,6 +215,15 @@ def dw_debug_basis(ctx, rhs: int, V_out=None, Z_out=None, H_out=None, max_cols: 
     _check(_lib.dw_debug_basis(ctx, int(rhs), _ptr(V_out), _ptr(Z_out), _ptr(H_out), int(max_cols), ctypes.byref(n)),
            "dw_debug_basis")
     return n.value
+
+
+def dw_residual_history(ctx, rhs: int = 0):
+    """[(steps, implicit rel. residual, explicit rel. residual)] per cycle of the last solve."""
+    n = _I(0)
+    _check(_lib.dw_residual_history(ctx, int(rhs), None, 0, ctypes.byref(n)), "dw_residual_history")
+    buf = (ctypes.c_double * (3 * max(1, n.value)))()
+    _check(_lib.dw_residual_history(ctx, int(rhs), buf, n.value, ctypes.byref(n)), "dw_residual_history")
+    return [(int(buf[3 * i]), buf[3 * i + 1], buf[3 * i + 2]) for i in range(n.value)]
 
 
 def dw_kernel_launches() -> int:

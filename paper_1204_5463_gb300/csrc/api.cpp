@@ -364,6 +364,11 @@ int dw_cancel(dw_ctx* ctx) {
     return DW_OK;
 }
 
+int dw_residual_history(dw_ctx* ctx, int rhs, double* out, int max, int* n) {
+    if (!ctx || !n || max < 0) return fail(DW_EINVAL, "bad argument");
+    return residual_history(ctx, rhs, out, max, n);
+}
+
 int dw_debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols) {
     if (!ctx || !ncols) return fail(DW_EINVAL, "null argument");
     return debug_basis(ctx, rhs, V_out, Z_out, H_out, max_cols, ncols);

@@ -245,6 +245,8 @@ int solve_checked(dw_ctx* ctx, const double* b, double* x, const dw_solver_param
                   const std::atomic<int>* cancel);
 int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw_stats* S,
           const std::atomic<int>* cancel);
+// the per-cycle residual history of the last solve on ctx (see dw_residual_history)
+int residual_history(dw_ctx* ctx, int rhs, double* out, int max, int* n);
 // the basis of the last cycle of the last solve on ctx (see dw_debug_basis)
 int debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols);
 

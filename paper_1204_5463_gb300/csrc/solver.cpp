@@ -51,6 +51,7 @@ struct RhsState {
     GivensLS ls;
     double bnorm = 0, rnorm = 0, res_impl = 0, wn0 = 0;
     int iterations = 0, cycles = 0, clean_restarts = 0;
+    std::vector<double> hist;  // per cycle end: steps, implicit and explicit relative residual
 };
 
 struct Solver {
@@ -143,6 +144,7 @@ struct Workspace {
     long long last_fv = 0, last_zb = 0;
     std::vector<int> last_mm;
     std::vector<std::vector<zd>> last_H;
+    std::vector<std::vector<double>> last_hist;  // per rhs: (steps, implicit, explicit) per cycle
     double2* dots_h = nullptr;
     double* norm2_h = nullptr;
     int* jtab_h = nullptr;
@@ -449,6 +451,9 @@ int Solver::cycle_end(int r) {
     DW_CUDA_TRY(cudaMemcpyAsync(norm2_h + r, norm2d + r, sizeof(double), cudaMemcpyDeviceToHost, st));
     if ((rc = sync())) return rc;
     s.rnorm = std::sqrt(norm2_h[r]);
+    s.hist.push_back((double)s.iterations);
+    s.hist.push_back(s.bnorm > 0 ? s.res_impl / s.bnorm : 0.0);
+    s.hist.push_back(s.bnorm > 0 ? s.rnorm / s.bnorm : 0.0);
     if (!std::isfinite(s.rnorm)) {
         s.done = true;
         s.status = DW_ENONFINITE;
@@ -728,9 +733,11 @@ int Solver::run(const double* b_user, double* x_user, dw_stats* S, const std::at
     W->last_zb = zb;
     W->last_mm.assign(nrhs, 0);
     W->last_H.assign(nrhs, std::vector<zd>());
+    W->last_hist.assign(nrhs, std::vector<double>());
     for (int r = 0; r < nrhs; ++r) {
         W->last_mm[r] = (R[r].j < 0) ? R[r].mm : 0;  // a cycle stopped mid-way has no consistent basis
         W->last_H[r] = R[r].H;
+        W->last_hist[r] = R[r].hist;
     }
     int status = DW_OK, conv = 0;
     for (auto& s : R) {
@@ -766,6 +773,17 @@ int solve(dw_ctx* ctx, const double* b, double* x, const dw_solver_params* P, dw
     int rc = s.setup();
     if (rc) return rc;
     return s.run(b, x, S, cancel);
+}
+
+int residual_history(dw_ctx* ctx, int rhs, double* out, int max, int* n) {
+    Workspace* W = ctx->ws;
+    if (!W || W->last_nrhs == 0) return fail(DW_EINVAL, "no solve has run on this context");
+    if (rhs < 0 || rhs >= W->last_nrhs) return fail(DW_EINVAL, "rhs out of range");
+    const std::vector<double>& h = W->last_hist[rhs];
+    *n = (int)(h.size() / 3);
+    if (out)
+        for (int i = 0; i < 3 * std::min(*n, max); ++i) out[i] = h[i];
+    return DW_OK;
 }
 
 int debug_basis(dw_ctx* ctx, int rhs, double* V_out, double* Z_out, double* H_out, int max_cols, int* ncols) {

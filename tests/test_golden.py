@@ -75,5 +75,13 @@ def test_cuda_fp64_path_reproduces_golden():
         xh = x.cpu().numpy().view(np.complex128)
         assert abs(np.linalg.norm(xh) - g["x_norm"]) <= 1e-9 * g["x_norm"]
         assert np.abs(xh[:24] - cplx(g["x_head"])).max() <= 1e-8 * np.abs(cplx(g["x_head"])).max()
+        # the per-cycle residual history (the paper's plots): the same cycle
+        # ends; implicit and explicit residuals agree while they lie well above
+        # the rounding of the two Gram-Schmidt variants (MGS printed, CGS here)
+        hist = dw.dw_residual_history(ctx, 0)
+        assert [h[0] for h in hist] == [hg[0] for hg in g["history"]]
+        for h, hg in zip(hist, g["history"]):
+            for a, e in ((h[1], hg[1]), (h[2], hg[2])):
+                assert abs(a - e) <= 1e-3 * e + 1e-13
     finally:
         dw.dw_destroy(ctx)
