@@ -23,8 +23,9 @@ using Key = std::tuple<int, int, int, int, int, int, int, int, int, int, int>;
 
 std::mutex g_mu;
 std::map<Key, std::vector<int>> g_cache;
-std::map<Key, std::vector<int>> g_sap_cache;  // (cycles, mr) per lattice, block in the key's place of the
-                                             // SAP parameters
+// (cycles, mr) per lattice, block, rhs count, precisions, m and k
+using SapKey = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, int>;
+std::map<SapKey, std::vector<int>> g_sap_cache;
 
 Key make_key(const dw_lattice* L, const dw_solver_params* P) {
     return Key(L->dims[0], L->dims[1], L->dims[2], L->dims[3], P->nrhs, (int)P->sap_prec, (int)P->outer_prec, P->m,
@@ -147,8 +148,8 @@ extern "C" int dw_autotune_sap(const dw_lattice* L, const double* U, const doubl
     if (!L || !U || !b || !P || !best_cycles || !best_mr) return fail(DW_EINVAL, "null argument");
     long long V = 0;
     if (!lattice_volume(L->dims, kMaxSites, &V)) return fail(DW_EINVAL, "bad lattice extents");
-    const Key key(L->dims[0], L->dims[1], L->dims[2], L->dims[3], P->nrhs, (int)P->sap_prec, (int)P->outer_prec,
-                  P->m, P->k, L->block[0] + 1000 * L->block[1], L->block[2] + 1000 * L->block[3]);
+    const SapKey key(L->dims[0], L->dims[1], L->dims[2], L->dims[3], L->block[0], L->block[1], L->block[2],
+                     L->block[3], P->nrhs, (int)P->sap_prec, (int)P->outer_prec, P->m, P->k);
     {
         std::lock_guard<std::mutex> lock(g_mu);
         auto it = g_sap_cache.find(key);
@@ -205,6 +206,7 @@ extern "C" int dw_autotune_sap(const dw_lattice* L, const double* U, const doubl
             }
             if (status == DW_ECUDA || status == DW_ETIMEOUT) {
                 dw_destroy(ctx);
+                if (n_results) *n_results = cnt;
                 return status;
             }
         }
