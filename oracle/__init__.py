@@ -20,14 +20,18 @@ Flexible SAP-Preconditioning of GMRES in Lattice QCD Simulation"):
 * ``fgmresdr`` -- Algorithm 4 (F-GMRES-DR) with the harmonic Ritz extraction of
   Lemma 1a, the deflated restart of Eqs. "G_kplus1", "tildeV_Vplus1", "hatHk",
   and the explicit-residual injection and clean restart of Sec. 5.7. ``k = 0``
-  gives restarted FGMRES (Sec. 5.2-5.3).
+  gives restarted FGMRES (Sec. 5.2-5.3). ``fgmresdr_steps`` is the same
+  iteration as a generator over Arnoldi steps (``fgmresdr`` drives it).
 * ``tune_m0_schur``, ``tune_m0_arnoldi``, ``tune_m0`` -- the bare mass that
   puts the leftmost eigenvalue of D at a chosen real part delta, from the
   identity spec(D_m0) = spec(D_0) + m0 and the leftmost Ritz value of D_0
   (thick-restarted Arnoldi ``krylov_schur_edge``, a single Arnoldi process
-  ``arnoldi_ritz``, or ARPACK), each with the residual norm of its Ritz pair.
-  Not from the paper, which quotes kappa values of thermalised fields: these
-  set up the synthetic workloads near the critical mass of Sec. 6.
+  ``arnoldi_ritz``, or ARPACK), each with the residual norm of its Ritz pair;
+  ``harmonic_ritz_nearest`` -- the eigenvalues nearest the origin by harmonic
+  Ritz values (Lemma 1a) with the thick restart of GMRES-DR, used to place and
+  verify the smallest |eigenvalue| of each workload's D. Not from the paper,
+  which quotes kappa values of thermalised fields: these set up the synthetic
+  workloads near the critical mass of Sec. 6.
 
 Small dense steps use numpy.linalg library routines (lstsq, qr, eig, solve).
 Readings where the paper is silent are stated next to the code that takes them.
