@@ -457,9 +457,46 @@ __device__ __forceinline__ void su3_mul(const cx<C> u[9], const cx<C> h[3], cx<C
     }
 }
 
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+// paired FP32 forms of project/reconstruct: every factor is +-1 or +-i, so
+// each lane is one rounded multiply-add of an exact product, the same result
+// as the scalar code, in half the instructions (the +-i cases pair the
+// swapped components)
+__device__ __forceinline__ float2 f2(cx<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ float2 f2sw(cx<float> a) { return make_float2(a.im, a.re); }
+__device__ __forceinline__ cx<float> cxf(float2 a) { return mk<float>(a.x, a.y); }
+// a + (w.x * b.x, w.y * b.y)
+__device__ __forceinline__ cx<float> fma_pair(float2 w, float2 b, cx<float> a) { return cxf(__ffma2_rn(w, b, f2(a))); }
+#endif
+
 // upper two spin rows of (1 + SIGN gamma_MU) psi
-template <int MU, int SIGN, class C>
+template <int MU, int SIGN, class C, bool PACK = false>
 __device__ __forceinline__ void project(const cx<C> psi[12], cx<C> h0[3], cx<C> h1[3]) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    if constexpr (PACK && std::is_same<C, float>::value) {
+        const float s = (float)SIGN;
+        const float2 pp = make_float2(s, s), pm = make_float2(s, -s), mp = make_float2(-s, s),
+                     mm = make_float2(-s, -s);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cx<float> p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
+            if constexpr (MU == 0) {  // p0 - s i p3, p1 - s i p2
+                h0[c] = fma_pair(pm, f2sw(p3), p0);
+                h1[c] = fma_pair(pm, f2sw(p2), p1);
+            } else if constexpr (MU == 1) {  // p0 - s p3, p1 + s p2
+                h0[c] = fma_pair(mm, f2(p3), p0);
+                h1[c] = fma_pair(pp, f2(p2), p1);
+            } else if constexpr (MU == 2) {  // p0 - s i p2, p1 + s i p3
+                h0[c] = fma_pair(pm, f2sw(p2), p0);
+                h1[c] = fma_pair(mp, f2sw(p3), p1);
+            } else {  // p0 + s p2, p1 + s p3
+                h0[c] = fma_pair(pp, f2(p2), p0);
+                h1[c] = fma_pair(pp, f2(p3), p1);
+            }
+        }
+        return;
+    }
+#endif
     const C s = (C)SIGN;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -481,8 +518,34 @@ __device__ __forceinline__ void project(const cx<C> psi[12], cx<C> h0[3], cx<C> 
 }
 
 // acc += the four spin rows rebuilt from the multiplied upper rows k0, k1
-template <int MU, int SIGN, class C>
+template <int MU, int SIGN, class C, bool PACK = false>
 __device__ __forceinline__ void reconstruct(const cx<C> k0[3], const cx<C> k1[3], cx<C> acc[12]) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    if constexpr (PACK && std::is_same<C, float>::value) {
+        const float s = (float)SIGN;
+        const float2 pp = make_float2(s, s), pm = make_float2(s, -s), mp = make_float2(-s, s),
+                     mm = make_float2(-s, -s);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[c] = cxf(__fadd2_rn(f2(acc[c]), f2(k0[c])));
+            acc[3 + c] = cxf(__fadd2_rn(f2(acc[3 + c]), f2(k1[c])));
+            if constexpr (MU == 0) {  // lower = s i (k1, k0)
+                acc[6 + c] = fma_pair(mp, f2sw(k1[c]), acc[6 + c]);
+                acc[9 + c] = fma_pair(mp, f2sw(k0[c]), acc[9 + c]);
+            } else if constexpr (MU == 1) {  // lower = s (k1, -k0)
+                acc[6 + c] = fma_pair(pp, f2(k1[c]), acc[6 + c]);
+                acc[9 + c] = fma_pair(mm, f2(k0[c]), acc[9 + c]);
+            } else if constexpr (MU == 2) {  // lower = s i (k0, -k1)
+                acc[6 + c] = fma_pair(mp, f2sw(k0[c]), acc[6 + c]);
+                acc[9 + c] = fma_pair(pm, f2sw(k1[c]), acc[9 + c]);
+            } else {  // lower = s (k0, k1)
+                acc[6 + c] = fma_pair(pp, f2(k0[c]), acc[6 + c]);
+                acc[9 + c] = fma_pair(pp, f2(k1[c]), acc[9 + c]);
+            }
+        }
+        return;
+    }
+#endif
     const C s = (C)SIGN;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -507,10 +570,10 @@ __device__ __forceinline__ void reconstruct(const cx<C> k0[3], const cx<C> k1[3]
 template <int MU, int SIGN, class C, bool PACK = false>
 __device__ __forceinline__ void hop(const cx<C> psi[12], const cx<C> u[9], cx<C> acc[12]) {
     cx<C> h0[3], h1[3], k0[3], k1[3];
-    project<MU, SIGN, C>(psi, h0, h1);
+    project<MU, SIGN, C, PACK>(psi, h0, h1);
     su3_mul<C, (SIGN < 0), PACK>(u, h0, k0);
     su3_mul<C, (SIGN < 0), PACK>(u, h1, k1);
-    reconstruct<MU, SIGN, C>(k0, k1, acc);
+    reconstruct<MU, SIGN, C, PACK>(k0, k1, acc);
 }
 
 // ---------------------------------------------------------------------------
