@@ -147,8 +147,18 @@ __device__ __forceinline__ df df_add(df a, df b) {
     s.lo += a.lo + b.lo;
     return quick_two_sum(s.hi, s.lo);
 }
+// The products that feed an error-free sum are rounded on their own
+// (__fmul_rn): a plain product could be contracted with the following
+// addition into one FMA, and the TwoSum after it would no longer be exact.
+__device__ __forceinline__ float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
 __device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = a.hi * b.hi;
+    const float p = mul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
@@ -158,7 +168,7 @@ __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
 // acc += a * b with a lazily normalised accumulator (acc.lo collects the
 // rounding errors; call df_norm before use)
 __device__ __forceinline__ void df_mac(df& acc, df a, df b) {
-    const float p = a.hi * b.hi;
+    const float p = mul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
@@ -168,7 +178,7 @@ __device__ __forceinline__ void df_mac(df& acc, df a, df b) {
 }
 // acc += a * b with b a plain FP32 number
 __device__ __forceinline__ void df_mac_f(df& acc, df a, float b) {
-    const float p = a.hi * b;
+    const float p = mul_rn(a.hi, b);
     float e = fmaf(a.hi, b, -p);
     e = fmaf(a.lo, b, e);
     const df s = two_sum(acc.hi, p);
