@@ -586,8 +586,14 @@ int Solver::step() {
         jtab_up[r] = jtab_h[r];
         norm2_up[r] = norm2_h[r];
     }
-    DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_up, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-    DW_CUDA_TRY(cudaMemcpyAsync(norm2d, norm2_up, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    if (need2) {
+        // without a second pass the device still holds this step's column
+        // table and the norms just read back: the uploads are needed only
+        // after a second pass changed them (this is the one host round trip
+        // of a step, so every call saved shortens the GPU's idle gap)
+        DW_CUDA_TRY(cudaMemcpyAsync(jtab_d, jtab_up, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+        DW_CUDA_TRY(cudaMemcpyAsync(norm2d, norm2_up, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    }
     {
         ProfScope ps(&ctx->prof, "normalize", (double)nact * (2.0 * fv + sb));
         if ((rc = launch_normalize(vp, vref_all(0, 1), vref_all(0, 1), V, jtab_d, nrhs, norm2d, sp, Lf, st)))
