@@ -131,13 +131,23 @@ struct Solver {
         DW_CUDA_TRY(cudaStreamSynchronize(st));
         return sap_check(ctx);
     }
+    // the step's dot rows and norms, read back with one copy (the norms follow
+    // the rows in the same device buffer), then a synchronisation
+    int read_dots_norms() {
+        DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP + sizeof(double) * nrhs,
+                                    cudaMemcpyDeviceToHost, st));
+        const int rc = sync();
+        if (rc) return rc;
+        std::memcpy(norm2_h, reinterpret_cast<const double*>(dots_h + (size_t)nrhs * NP), sizeof(double) * nrhs);
+        return DW_OK;
+    }
 };
 
 }  // namespace
 
 // Workspace kept by the context between solves (grown on demand).
 struct Workspace {
-    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, norm2, scal, jtab, nz, canon, cnt, bscale;
+    DevBuf V, Z, x, b, r, vlow, zscr, rlow, zsap, partial, dots, Q, eta, scal, jtab, nz, canon, cnt, bscale;
     // the last solve's bases as dw_debug_basis reads them: formats, sizes and,
     // per rhs, the columns and the (m+1) x m Hessenberg-like matrix of its last cycle
     int last_nrhs = 0, last_m = 0, last_vp = -1, last_zp = -1;
@@ -168,7 +178,7 @@ static Workspace* workspace_of(dw_ctx* ctx) {
         if (ctx->ws)
             for (DevBuf* b : {&ctx->ws->V, &ctx->ws->Z, &ctx->ws->x, &ctx->ws->b, &ctx->ws->r, &ctx->ws->vlow,
                               &ctx->ws->zscr, &ctx->ws->rlow, &ctx->ws->zsap, &ctx->ws->partial, &ctx->ws->dots, &ctx->ws->Q, &ctx->ws->eta,
-                              &ctx->ws->norm2, &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon,
+                              &ctx->ws->scal, &ctx->ws->jtab, &ctx->ws->nz, &ctx->ws->canon,
                               &ctx->ws->cnt, &ctx->ws->bscale})
                 b->st = ctx->stream;
     }
@@ -221,7 +231,6 @@ int Solver::setup() {
     if ((rc = W->dots.ensure((size_t)2 * nrhs * NP * sizeof(double2)))) return rc;
     if ((rc = W->Q.ensure((size_t)(m + 1) * (m + 1) * sizeof(double2)))) return rc;
     if ((rc = W->eta.ensure((size_t)(m + 1) * sizeof(double2)))) return rc;
-    if ((rc = W->norm2.ensure((size_t)nrhs * sizeof(double)))) return rc;
     if ((rc = W->scal.ensure((size_t)nrhs * sizeof(double)))) return rc;
     if ((rc = W->jtab.ensure((size_t)nrhs * sizeof(int)))) return rc;
     if ((rc = W->nz.ensure(sizeof(int)))) return rc;
@@ -258,7 +267,9 @@ int Solver::setup() {
     dots = W->dots.as<double2>();
     Qd = W->Q.as<double2>();
     etad = W->eta.as<double2>();
-    norm2d = W->norm2.as<double>();
+    // the norms follow the dots in one buffer, so that a step reads both back
+    // with one copy (the dot rows take the first nrhs * NP entries)
+    norm2d = reinterpret_cast<double*>(dots + (size_t)nrhs * NP);
     scal_d = W->scal.as<double>();
     jtab_d = W->jtab.as<int>();
     nz_d = W->nz.as<int>();
@@ -532,9 +543,7 @@ int Solver::step() {
                                    norm2d, st, cnt_d)))
             return rc;
     }
-    DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
-    DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-    if ((rc = sync())) return rc;
+    if ((rc = read_dots_norms())) return rc;
     // unit roundoff of the basis format, and the orthogonality level below
     // which a second pass is taken (FP64-class: 1e-13; FP32: 1e-5)
     const double unit = (vp == P32) ? 5.960464477539063e-08 : (vp == PDF) ? 3.552713678800501e-15
@@ -569,9 +578,7 @@ int Solver::step() {
                                        nblk, norm2d, st, cnt_d)))
                 return rc;
         }
-        DW_CUDA_TRY(cudaMemcpyAsync(dots_h, dots, sizeof(double2) * nrhs * NP, cudaMemcpyDeviceToHost, st));
-        DW_CUDA_TRY(cudaMemcpyAsync(norm2_h, norm2d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-        if ((rc = sync())) return rc;
+        if ((rc = read_dots_norms())) return rc;
         for (int r = 0; r < nrhs; ++r) {
             if (jtab_h[r] < 0) {
                 norm2_h[r] = keep[r];
